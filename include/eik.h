@@ -1,0 +1,193 @@
+/*
+ * eik.h -- C ABI of the GB300 (sm_103a) Eikonal solver libeik.so.
+ *
+ * The library solves the first-order upwind (Godunov) discretization of the
+ * static Eikonal equation |grad u(x)| F(x) = 1 with u = q on an exit set
+ * (Chacon & Vladimirsky, "A parallel Heap-Cell Method for Eikonal
+ * equations", arXiv:1306.4743, Sec. 1.1, Eq. 2) on a uniform 3D grid, by a
+ * GPU restatement of the parallel Heap-Cell Method (Sec. 4-5, Alg. 1-3):
+ * the grid is split into cells of n^3 nodes, each cell is swept with the
+ * modified Locking Sweeping update of Alg. 2 in alternating directions,
+ * cells whose border values changed are flagged, and a persistent kernel
+ * takes the next cells from a device-side bucketed queue keyed on the cell
+ * value of Eq. 3.
+ *
+ * Grid convention (Sec. 1.1): node (i,j,k), 0 <= i < nx, 0 <= j < ny,
+ * 0 <= k < nz, sits at (i h, j h, k h); every array below holds one entry
+ * per node at linear index i + nx*(j + ny*k) (i fastest).  Values outside
+ * the grid are +infinity (Sec. 1.1); exit nodes (the set Q' of Sec. 4) keep
+ * u = q exactly.
+ *
+ * Ownership: the caller owns every input and output buffer; the library
+ * copies what it needs during a call and keeps no caller pointer after the
+ * call returns (for eik_submit: after eik_poll reports completion).  The
+ * library owns an eik_ctx and all device memory inside it.
+ *
+ * Errors: every entry point returns an eik_status code; nothing aborts the
+ * process.  A device wait that exceeds opts.spin_cap_us, or a device fault,
+ * surfaces as EIK_ETIMEOUT / EIK_ECUDA.  eik_strerror() names each code.
+ *
+ * Threads: one eik_ctx may be used by one host thread at a time.
+ */
+#ifndef EIK_H
+#define EIK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque solver context (owned by the library). */
+typedef struct eik_ctx eik_ctx;
+
+/* Status codes. */
+enum {
+  EIK_OK = 0,
+  EIK_EINVAL = 1,     /* bad argument: dims < 1, h <= 0, F <= 0 or not finite,
+                         no exit node, q not finite, tol < 0 or NaN */
+  EIK_ENOMEM = 2,     /* device or host allocation failed */
+  EIK_EBUDGET = 3,    /* the solve needs more device memory than
+                         opts.hbm_budget_bytes allows */
+  EIK_ECUDA = 4,      /* a CUDA call failed */
+  EIK_ETIMEOUT = 5,   /* a device wait passed opts.spin_cap_us without progress */
+  EIK_ENOCONV = 6,    /* a cell passed the sweep limit of one visit */
+  EIK_ECANCELLED = 7, /* a submitted request was cancelled */
+  EIK_EQUEUE = 8,     /* internal device queue inconsistency */
+  EIK_ENOTFOUND = 9   /* unknown ticket */
+};
+
+/* Arithmetic of the sweeps. */
+typedef enum {
+  EIK_FP64 = 0,        /* every sweep in double precision */
+  EIK_FP32_POLISH = 1  /* bulk sweeps in single precision, then double
+                          precision polishing sweeps from the single-precision
+                          result (Sec. 6.5 studies the single-precision
+                          behaviour; the polish restores double precision) */
+} eik_precision;
+
+/* Options of a context.  Fill with eik_opts_default() and change fields. */
+typedef struct {
+  int device;               /* CUDA device ordinal (default 0) */
+  int precision;            /* eik_precision (default EIK_FP32_POLISH) */
+  int cell_n;               /* nodes per cell side: 4, 8 or 16; 0 = choose by
+                               the built-in size table (default 0) */
+  int reserved;             /* must be 0 */
+  size_t hbm_budget_bytes;  /* device-memory limit of this context; 0 = none */
+  uint64_t spin_cap_us;     /* longest device wait without global progress,
+                               in microseconds (default 5,000,000); 0 makes
+                               every idle wait fail at once (test hook) */
+  double bucket_width;      /* width of one queue bucket in units of
+                               (cell edge x mean slowness); <= 0 = default 1 */
+  int max_sweeps_per_visit; /* sweep limit of one cell visit (default 4096) */
+  int reserved2;            /* must be 0 */
+} eik_opts;
+
+/* Counters and results of one solve (of the whole batch for batch calls). */
+typedef struct {
+  double seconds;               /* device time from the first init kernel to
+                                   the final u on the device */
+  uint64_t cell_visits;         /* cells taken from the queue, bulk pass */
+  uint64_t sweeps;              /* directional sweeps, bulk pass */
+  uint64_t node_updates;        /* local solves, bulk pass */
+  uint64_t polish_visits;       /* cells taken from the queue, FP64 polish */
+  uint64_t polish_sweeps;
+  uint64_t polish_node_updates;
+  uint64_t queue_pushes;        /* bucket insertions, both passes */
+  uint64_t nonfinite;           /* nodes left non-finite (0 on success) */
+  uint64_t nodes;               /* nx*ny*nz summed over instances */
+  int cell_n_used;
+  int precision_used;
+  double residual_max;          /* max |u - Lambda(u)| over non-exit nodes,
+                                   recomputed in FP64 after the solve */
+  double u_max;                 /* largest finite u */
+  double seconds_bulk;          /* device time of the bulk cell kernel */
+  double seconds_polish;        /* device time of the polish cell kernel */
+} eik_stats;
+
+/* Default options. */
+int eik_opts_default(eik_opts *opts);
+
+/* Create a context on opts->device (NULL opts = defaults).  *out is set to a
+ * new context on success and to NULL on failure. */
+int eik_create(eik_ctx **out, const eik_opts *opts);
+
+/* Free a context and its device memory.  NULL is accepted. */
+int eik_destroy(eik_ctx *ctx);
+
+/* Static English text for a status code. */
+const char *eik_strerror(int status);
+
+/*
+ * Solve one grid (Eq. 2), host buffers.
+ *   dims[3]  = {nx, ny, nz}, each >= 1
+ *   h        = grid step, > 0
+ *   F        = speed per node (nx*ny*nz floats), > 0 and finite off the exit set
+ *   src_mask = exit set Q' (nx*ny*nz bytes), nonzero = exit node; at least one
+ *   q        = exit values (nx*ny*nz doubles), read only where src_mask != 0,
+ *              finite
+ *   tol      = kappa of the early-termination rule of Sec. 6.4: a local
+ *              update that changes a value by no more than tol does not count
+ *              as a change, neither for stopping a cell's sweeps nor for
+ *              flagging a neighbouring cell (tol = 0: sweep until no value
+ *              changes).  Applies to the FP64 sweeps of either precision mode.
+ *   u_out    = caller-owned nx*ny*nz doubles, written on EIK_OK
+ *   stats    = may be NULL
+ * Returns EIK_OK or an error code; on error u_out is unspecified.
+ */
+int eik_solve(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
+              const uint8_t *src_mask, const double *q, double tol,
+              double *u_out, eik_stats *stats);
+
+/*
+ * Same as eik_solve with every array in device memory of ctx's device.
+ * The work runs on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream) and the call returns after the stream has finished it.
+ */
+int eik_solve_device(eik_ctx *ctx, const int64_t dims[3], double h,
+                     const float *F_dev, const uint8_t *src_mask_dev,
+                     const double *q_dev, double tol, double *u_out_dev,
+                     void *stream, eik_stats *stats);
+
+/*
+ * Solve `count` independent grids in one persistent launch (host buffers).
+ * Instance t uses dims[3t..3t+2], h[t], F[t], src_mask[t], q[t], u_out[t].
+ * Cells of all instances share one device queue.  stats (may be NULL) sums
+ * over the batch.
+ */
+int eik_solve_batch(eik_ctx *ctx, int count, const int64_t *dims,
+                    const double *h, const float *const *F,
+                    const uint8_t *const *src_mask, const double *const *q,
+                    double tol, double *const *u_out, eik_stats *stats);
+
+/* Device-buffer variant of eik_solve_batch (all arrays in device memory;
+ * the pointer tables themselves are host arrays). */
+int eik_solve_batch_device(eik_ctx *ctx, int count, const int64_t *dims,
+                           const double *h, const float *const *F_dev,
+                           const uint8_t *const *src_mask_dev,
+                           const double *const *q_dev, double tol,
+                           double *const *u_out_dev, void *stream,
+                           eik_stats *stats);
+
+/*
+ * Serving.  eik_submit queues one solve (host buffers, same arguments as
+ * eik_solve) and returns a ticket at once; the library copies the inputs
+ * before returning.  Requests are admitted to the device in arrival order
+ * while their memory fits the context budget, run together with the
+ * requests already on the device, and write u_out when done.  eik_poll
+ * advances the device work and sets *done = 1 once the ticket's u_out is
+ * written (its status is then returned).  eik_cancel drops a ticket that
+ * has not completed.
+ */
+int eik_submit(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
+               const uint8_t *src_mask, const double *q, double tol,
+               double *u_out, uint64_t *ticket);
+int eik_poll(eik_ctx *ctx, uint64_t ticket, int *done, eik_stats *stats);
+int eik_cancel(eik_ctx *ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIK_H */

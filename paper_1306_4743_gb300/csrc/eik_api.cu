@@ -1,0 +1,645 @@
+// eik_api.cu -- host runtime and C ABI of libeik.so (declared in
+// include/eik.h): contexts, device memory, tensor maps, the launch sequence
+// of one (batched) solve, statistics, and the serving queue.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "eik.h"
+#include "eik_internal.h"
+#include "eik_prep.h"
+#include "eik_serve.h"
+
+using namespace eik;
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int box_width(int n, int es) { return (((n + 2) * es + 15) / 16) * 16 / es; }
+
+long long padded_x(int nx, int n, int ncx, int es) {
+  long long need = (long long)n * (ncx - 1) + box_width(n, es);
+  if (need < nx + 2) need = nx + 2;
+  return (long long)align_up((size_t)need, 8);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context.
+struct eik_ctx {
+  eik_opts opts;
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  EncodeTiledFn encode = nullptr;
+  // grow-only device arena
+  char* arena = nullptr;
+  size_t arena_size = 0;
+  // plane tables, per cell size (index 0: n=4, 1: n=8, 2: n=16)
+  unsigned short* d_tab[3] = {nullptr, nullptr, nullptr};
+  int* d_off[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {};
+  // host staging of small tables (pinned)
+  char* h_small = nullptr;
+  size_t h_small_size = 0;
+  // serving
+  ServeState* serve = nullptr;
+  // autotune cache: log2(nodes) bucket -> cell size
+  std::map<int, int> tuned;
+};
+
+namespace {
+
+int size_index(int n) { return n == 4 ? 0 : n == 8 ? 1 : n == 16 ? 2 : -1; }
+
+cudaError_t ensure_plane_table(eik_ctx* ctx, int n) {
+  const int si = size_index(n);
+  if (ctx->d_tab[si]) return cudaSuccess;
+  const int n3 = n * n * n, np = 3 * (n - 1) + 1;
+  std::vector<unsigned short> tab;
+  std::vector<int> off(np + 1, 0);
+  tab.reserve(n3);
+  for (int C = 0; C < np; ++C) {
+    off[C] = (int)tab.size();
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b) {
+        const int a = C - b - c;
+        if (a >= 0 && a < n) tab.push_back((unsigned short)(a | (b << 5) | (c << 10)));
+      }
+  }
+  off[np] = (int)tab.size();
+  cudaError_t e = cudaMalloc(&ctx->d_tab[si], n3 * sizeof(unsigned short));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&ctx->d_off[si], (np + 1) * sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(ctx->d_tab[si], tab.data(), n3 * sizeof(unsigned short), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(ctx->d_off[si], off.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice);
+}
+
+// Layout of one instance inside a launch.
+struct InstPlan {
+  int nx, ny, nz;
+  double h;
+  int ncx, ncy, ncz, ncells, cell_base;
+  long long px_b, px64, py, pz;
+  size_t off_ub, off_sb, off_u64, off_s64, off_F, off_mask, off_q, off_out;
+  long long nodes;
+};
+
+// Sub-allocation of the arena for one launch.
+struct LaunchPlan {
+  int count = 0;
+  int n = 8;
+  bool polish = false;  // FP32 bulk + FP64 polish
+  std::vector<InstPlan> inst;
+  int total_cells = 0, max_cells = 0;
+  long long max_padded_b = 0, max_padded64 = 0, max_cellnodes = 0, max_nodes = 0;
+  size_t off_key, off_state, off_dir, off_inst, off_next, off_heads, off_ctl, off_nsrc;
+  size_t off_inst_b, off_inst64, off_tmap_b, off_tmap64, off_prep, off_pol, off_fin;
+  size_t total = 0;
+  size_t small_begin = 0, small_end = 0;  // tables copied from the host in one go
+};
+
+size_t take(size_t& cursor, size_t bytes) {
+  const size_t at = align_up(cursor, 256);
+  cursor = at + align_up(bytes, 256);
+  return at;
+}
+
+int choose_cell_n(eik_ctx* ctx, long long nodes) {
+  if (ctx->opts.cell_n) return ctx->opts.cell_n;
+  int lg = 0;
+  while ((1ll << (lg + 1)) <= nodes) ++lg;
+  auto it = ctx->tuned.find(lg);
+  if (it != ctx->tuned.end()) return it->second;
+  return 8;
+}
+
+void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, int n, bool polish,
+               bool host_io) {
+  L.count = count;
+  L.n = n;
+  L.polish = polish;
+  L.inst.resize(count);
+  const int es_b = polish ? 4 : 8;
+  size_t cur = 0;
+  int cells = 0;
+  for (int t = 0; t < count; ++t) {
+    InstPlan& I = L.inst[t];
+    I.nx = (int)dims[3 * t];
+    I.ny = (int)dims[3 * t + 1];
+    I.nz = (int)dims[3 * t + 2];
+    I.h = h[t];
+    I.ncx = (I.nx + n - 1) / n;
+    I.ncy = (I.ny + n - 1) / n;
+    I.ncz = (I.nz + n - 1) / n;
+    I.ncells = I.ncx * I.ncy * I.ncz;
+    I.cell_base = cells;
+    cells += I.ncells;
+    I.py = (long long)n * I.ncy + 2;
+    I.pz = (long long)n * I.ncz + 2;
+    I.px_b = padded_x(I.nx, n, I.ncx, es_b);
+    I.px64 = padded_x(I.nx, n, I.ncx, 8);
+    I.nodes = (long long)I.nx * I.ny * I.nz;
+    const long long cn = (long long)I.ncells * n * n * n;
+    I.off_ub = take(cur, (size_t)(I.px_b * I.py * I.pz) * es_b);
+    I.off_sb = take(cur, (size_t)cn * es_b);
+    if (polish) {
+      I.off_u64 = take(cur, (size_t)(I.px64 * I.py * I.pz) * 8);
+      I.off_s64 = take(cur, (size_t)cn * 8);
+    } else {
+      I.off_u64 = I.off_ub;
+      I.off_s64 = I.off_sb;
+    }
+    if (host_io) {
+      I.off_F = take(cur, (size_t)I.nodes * 4);
+      I.off_mask = take(cur, (size_t)I.nodes);
+      I.off_q = take(cur, (size_t)I.nodes * 8);
+      I.off_out = take(cur, (size_t)I.nodes * 8);
+    } else {
+      I.off_F = I.off_mask = I.off_q = I.off_out = 0;
+    }
+    L.max_cells = std::max(L.max_cells, I.ncells);
+    L.max_padded_b = std::max(L.max_padded_b, I.px_b * I.py * I.pz);
+    L.max_padded64 = std::max(L.max_padded64, I.px64 * I.py * I.pz);
+    L.max_cellnodes = std::max(L.max_cellnodes, cn);
+    L.max_nodes = std::max(L.max_nodes, I.nodes);
+  }
+  L.total_cells = cells;
+  L.off_key = take(cur, (size_t)cells * 4);
+  L.off_state = take(cur, (size_t)cells * 4);
+  L.off_dir = take(cur, (size_t)cells * 4);
+  L.off_inst = take(cur, (size_t)cells * 4);
+  L.off_next = take(cur, (size_t)cells * 4);
+  L.off_heads = take(cur, (size_t)kNumBuckets * 8);
+  // small tables, filled on the host and copied in one transfer
+  L.small_begin = align_up(cur, 256);
+  L.off_ctl = take(cur, sizeof(Control));
+  L.off_nsrc = take(cur, (size_t)count * 4);
+  L.off_inst_b = take(cur, (size_t)count * sizeof(Instance));
+  L.off_inst64 = take(cur, (size_t)count * sizeof(Instance));
+  L.off_tmap_b = take(cur, (size_t)count * sizeof(CUtensorMap));
+  L.off_tmap64 = take(cur, (size_t)count * sizeof(CUtensorMap));
+  L.off_prep = take(cur, (size_t)count * sizeof(PrepInstance));
+  L.off_pol = take(cur, (size_t)count * sizeof(PolishInstance));
+  L.off_fin = take(cur, (size_t)count * sizeof(FinalInstance));
+  L.small_end = align_up(cur, 256);
+  L.total = L.small_end;
+}
+
+int ensure_arena(eik_ctx* ctx, size_t bytes) {
+  if (ctx->opts.hbm_budget_bytes && bytes > ctx->opts.hbm_budget_bytes) return EIK_EBUDGET;
+  if (bytes <= ctx->arena_size) return EIK_OK;
+  if (ctx->arena) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_size = 0;
+  }
+  size_t want = align_up(bytes + bytes / 8, 1 << 20);
+  if (ctx->opts.hbm_budget_bytes && want > ctx->opts.hbm_budget_bytes) want = bytes;
+  if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return EIK_ENOMEM;
+    }
+    want = bytes;
+  }
+  ctx->arena_size = want;
+  return EIK_OK;
+}
+
+int ensure_host_small(eik_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->h_small_size) return EIK_OK;
+  if (ctx->h_small) cudaFreeHost(ctx->h_small);
+  ctx->h_small = nullptr;
+  ctx->h_small_size = 0;
+  if (cudaMallocHost(&ctx->h_small, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return EIK_ENOMEM;
+  }
+  ctx->h_small_size = bytes;
+  return EIK_OK;
+}
+
+int encode_map(eik_ctx* ctx, CUtensorMap* map, void* base, int es, long long px, long long py,
+               long long pz, int n) {
+  const cuuint64_t gdim[3] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(px * es), (cuuint64_t)(px * py * es)};
+  const cuuint32_t box[3] = {(cuuint32_t)box_width(n, es), (cuuint32_t)(n + 2),
+                             (cuuint32_t)(n + 2)};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  CUresult r = ctx->encode(map, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                           3, base, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? EIK_OK : EIK_ECUDA;
+}
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) {               \
+      cudaGetLastError();                  \
+      return EIK_ECUDA;                    \
+    }                                      \
+  } while (0)
+
+bool valid_dims(const int64_t* d) {
+  for (int a = 0; a < 3; ++a)
+    if (d[a] < 1 || d[a] > (1 << 24)) return false;
+  const long long nodes = (long long)d[0] * d[1] * d[2];
+  return nodes <= (1ll << 34);
+}
+
+}  // namespace
+
+// Launch sequence of one batched solve.  IO arrays are host pointers when
+// host_io, else device pointers.  Leaves results in u_out (host or device).
+int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
+                  const float* const* F, const uint8_t* const* mask, const double* const* q,
+                  double tol, double* const* u_out, bool host_io, cudaStream_t st,
+                  eik_stats* stats, int n_override) {
+  if (!ctx || count < 1 || !dims || !h || !F || !mask || !q || !u_out) return EIK_EINVAL;
+  if (!(tol >= 0.0) || isinf(tol)) return EIK_EINVAL;
+  long long nodes_total = 0, nodes_max = 0;
+  for (int t = 0; t < count; ++t) {
+    if (!valid_dims(dims + 3 * t)) return EIK_EINVAL;
+    if (!(h[t] > 0.0) || isinf(h[t])) return EIK_EINVAL;
+    if (!F[t] || !mask[t] || !q[t] || !u_out[t]) return EIK_EINVAL;
+    const long long nd = (long long)dims[3 * t] * dims[3 * t + 1] * dims[3 * t + 2];
+    nodes_total += nd;
+    nodes_max = std::max(nodes_max, nd);
+  }
+  const bool polish = ctx->opts.precision == EIK_FP32_POLISH;
+  const int n = n_override ? n_override : choose_cell_n(ctx, nodes_max);
+  if (size_index(n) < 0) return EIK_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(ensure_plane_table(ctx, n));
+
+  LaunchPlan L;
+  make_plan(L, count, dims, h, n, polish, host_io);
+  if (L.total_cells > (1 << 30)) return EIK_EINVAL;
+  int rc = ensure_arena(ctx, L.total);
+  if (rc) return rc;
+  rc = ensure_host_small(ctx, L.small_end - L.small_begin);
+  if (rc) return rc;
+  char* A = ctx->arena;
+
+  // host-side small tables
+  char* hs = ctx->h_small;
+  memset(hs, 0, L.small_end - L.small_begin);
+  auto hptr = [&](size_t off) { return hs + (off - L.small_begin); };
+  Control* hctl = reinterpret_cast<Control*>(hptr(L.off_ctl));
+  hctl->min_q_ord = ~0ull;
+  Instance* hib = reinterpret_cast<Instance*>(hptr(L.off_inst_b));
+  Instance* hi64 = reinterpret_cast<Instance*>(hptr(L.off_inst64));
+  CUtensorMap* htb = reinterpret_cast<CUtensorMap*>(hptr(L.off_tmap_b));
+  CUtensorMap* ht64 = reinterpret_cast<CUtensorMap*>(hptr(L.off_tmap64));
+  PrepInstance* hp = reinterpret_cast<PrepInstance*>(hptr(L.off_prep));
+  PolishInstance* hpol = reinterpret_cast<PolishInstance*>(hptr(L.off_pol));
+  FinalInstance* hfin = reinterpret_cast<FinalInstance*>(hptr(L.off_fin));
+  const int es_b = polish ? 4 : 8;
+  for (int t = 0; t < count; ++t) {
+    const InstPlan& I = L.inst[t];
+    Instance& b = hib[t];
+    b.u = A + I.off_ub;
+    b.s = A + I.off_sb;
+    b.px = I.px_b;
+    b.py = I.py;
+    b.pz = I.pz;
+    b.nx = I.nx;
+    b.ny = I.ny;
+    b.nz = I.nz;
+    b.ncx = I.ncx;
+    b.ncy = I.ncy;
+    b.ncz = I.ncz;
+    b.cell_base = I.cell_base;
+    b.ncells = I.ncells;
+    b.kappa = polish ? 0.0 : tol;
+    Instance& d = hi64[t];
+    d = b;
+    d.u = A + I.off_u64;
+    d.s = A + I.off_s64;
+    d.px = I.px64;
+    d.kappa = tol;
+    rc = encode_map(ctx, &htb[t], b.u, es_b, I.px_b, I.py, I.pz, n);
+    if (rc) return rc;
+    if (polish) {
+      rc = encode_map(ctx, &ht64[t], d.u, 8, I.px64, I.py, I.pz, n);
+      if (rc) return rc;
+    }
+    PrepInstance& P = hp[t];
+    P.F = host_io ? reinterpret_cast<const float*>(A + I.off_F) : F[t];
+    P.mask = host_io ? reinterpret_cast<const uint8_t*>(A + I.off_mask) : mask[t];
+    P.q = host_io ? reinterpret_cast<const double*>(A + I.off_q) : q[t];
+    P.h = I.h;
+    P.u = b.u;
+    P.s = A + I.off_sb;
+    P.s64 = polish ? (void*)(A + I.off_s64) : nullptr;
+    P.px = I.px_b;
+    P.py = I.py;
+    P.pz = I.pz;
+    P.nx = I.nx;
+    P.ny = I.ny;
+    P.nz = I.nz;
+    P.ncx = I.ncx;
+    P.ncy = I.ncy;
+    P.ncz = I.ncz;
+    P.cell_base = I.cell_base;
+    P.ncells = I.ncells;
+    P.n = n;
+    PolishInstance& Q = hpol[t];
+    Q.mask = P.mask;
+    Q.q = P.q;
+    Q.u32 = b.u;
+    Q.u64 = A + I.off_u64;
+    Q.s64 = A + I.off_s64;
+    Q.px32 = I.px_b;
+    Q.px64 = I.px64;
+    Q.py = I.py;
+    Q.pz = I.pz;
+    Q.nx = I.nx;
+    Q.ny = I.ny;
+    Q.nz = I.nz;
+    Q.ncx = I.ncx;
+    Q.ncy = I.ncy;
+    Q.ncz = I.ncz;
+    Q.cell_base = I.cell_base;
+    Q.ncells = I.ncells;
+    Q.n = n;
+    FinalInstance& Fi = hfin[t];
+    Fi.u64 = A + I.off_u64;
+    Fi.s64 = A + I.off_s64;
+    Fi.out = host_io ? reinterpret_cast<double*>(A + I.off_out) : u_out[t];
+    Fi.px64 = I.px64;
+    Fi.py = I.py;
+    Fi.pz = I.pz;
+    Fi.nx = I.nx;
+    Fi.ny = I.ny;
+    Fi.nz = I.nz;
+    Fi.ncx = I.ncx;
+    Fi.ncy = I.ncy;
+    Fi.ncz = I.ncz;
+    Fi.n = n;
+  }
+
+  // inputs and tables to the device
+  if (host_io) {
+    for (int t = 0; t < count; ++t) {
+      const InstPlan& I = L.inst[t];
+      CK(cudaMemcpyAsync(A + I.off_F, F[t], (size_t)I.nodes * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(A + I.off_mask, mask[t], (size_t)I.nodes, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(A + I.off_q, q[t], (size_t)I.nodes * 8, cudaMemcpyHostToDevice, st));
+    }
+  }
+  CK(cudaMemcpyAsync(A + L.small_begin, hs, L.small_end - L.small_begin, cudaMemcpyHostToDevice,
+                     st));
+  CK(cudaMemsetAsync(A + L.off_heads, 0, (size_t)kNumBuckets * 8, st));
+
+  CellArrays cells;
+  cells.key = reinterpret_cast<unsigned*>(A + L.off_key);
+  cells.state = reinterpret_cast<unsigned*>(A + L.off_state);
+  cells.dir = reinterpret_cast<unsigned*>(A + L.off_dir);
+  cells.inst = reinterpret_cast<int*>(A + L.off_inst);
+  cells.next = reinterpret_cast<unsigned*>(A + L.off_next);
+  cells.heads = reinterpret_cast<unsigned long long*>(A + L.off_heads);
+  Control* dctl = reinterpret_cast<Control*>(A + L.off_ctl);
+
+  CK(cudaEventRecord(ctx->ev[0], st));
+  double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 1.0;
+  CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), count,
+                      L.max_padded_b, L.max_cellnodes, L.max_cells, L.total_cells, cells, dctl,
+                      reinterpret_cast<int*>(A + L.off_nsrc), !polish, n, wf, ctx->sms, st));
+
+  CellKernelParams p;
+  p.inst = reinterpret_cast<const Instance*>(A + L.off_inst_b);
+  p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap_b);
+  p.cells = cells;
+  p.ctl = dctl;
+  p.plane_tab = ctx->d_tab[size_index(n)];
+  p.plane_off = ctx->d_off[size_index(n)];
+  p.spin_cap_ns = ctx->opts.spin_cap_us * 1000ull;
+  p.max_sweeps = ctx->opts.max_sweeps_per_visit;
+  p.pass = 0;
+  CK(cudaEventRecord(ctx->ev[1], st));
+  CK(launch_cells(!polish, false, n, p, ctx->sms, st, nullptr));
+  CK(cudaEventRecord(ctx->ev[2], st));
+  if (polish) {
+    CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), count,
+                          L.max_padded64, L.max_cells, L.total_cells, cells, dctl, ctx->sms, st));
+    p.inst = reinterpret_cast<const Instance*>(A + L.off_inst64);
+    p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap64);
+    p.pass = 1;
+    CK(cudaEventRecord(ctx->ev[3], st));
+    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
+    CK(cudaEventRecord(ctx->ev[4], st));
+  }
+  CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
+                             L.max_nodes, dctl, ctx->sms, st));
+  CK(cudaEventRecord(ctx->ev[5], st));
+  Control* hres = hctl;  // reuse the pinned staging for the read-back
+  CK(cudaMemcpyAsync(hres, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  if (host_io) {
+    for (int t = 0; t < count; ++t) {
+      const InstPlan& I = L.inst[t];
+      CK(cudaMemcpyAsync(u_out[t], A + I.off_out, (size_t)I.nodes * 8, cudaMemcpyDeviceToHost,
+                         st));
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+    stats->seconds = ms * 1e-3;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    stats->seconds_bulk = ms * 1e-3;
+    if (polish) {
+      cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]);
+      stats->seconds_polish = ms * 1e-3;
+    }
+    stats->cell_visits = hres->counters[0][kCntVisits];
+    stats->sweeps = hres->counters[0][kCntSweeps];
+    stats->node_updates = hres->counters[0][kCntUpdates];
+    stats->polish_visits = hres->counters[1][kCntVisits];
+    stats->polish_sweeps = hres->counters[1][kCntSweeps];
+    stats->polish_node_updates = hres->counters[1][kCntUpdates];
+    stats->queue_pushes = hres->counters[0][kCntPushes] + hres->counters[1][kCntPushes];
+    stats->nonfinite = hres->nonfinite;
+    stats->nodes = (uint64_t)nodes_total;
+    stats->cell_n_used = n;
+    stats->precision_used = polish ? EIK_FP32_POLISH : EIK_FP64;
+    double r;
+    unsigned long long rb = hres->resid_bits;
+    memcpy(&r, &rb, 8);
+    stats->residual_max = r;
+    unsigned long long ub = hres->umax_bits;
+    ub = (ub & 0x8000000000000000ull) ? (ub & 0x7fffffffffffffffull) : ~ub;
+    memcpy(&r, &ub, 8);
+    stats->u_max = hres->umax_bits ? r : 0.0;
+  }
+  if (hres->status) return hres->status;
+  if (hres->nonfinite) return EIK_ENOCONV;
+  return EIK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI.
+extern "C" {
+
+int eik_opts_default(eik_opts* o) {
+  if (!o) return EIK_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->device = 0;
+  o->precision = EIK_FP32_POLISH;
+  o->cell_n = 0;
+  o->hbm_budget_bytes = 0;
+  o->spin_cap_us = 5000000ull;
+  o->bucket_width = 1.0;
+  o->max_sweeps_per_visit = 4096;
+  return EIK_OK;
+}
+
+const char* eik_strerror(int s) {
+  switch (s) {
+    case EIK_OK: return "ok";
+    case EIK_EINVAL: return "invalid argument";
+    case EIK_ENOMEM: return "out of memory";
+    case EIK_EBUDGET: return "device memory budget exceeded";
+    case EIK_ECUDA: return "CUDA error";
+    case EIK_ETIMEOUT: return "device wait limit reached without progress";
+    case EIK_ENOCONV: return "cell sweeps did not converge";
+    case EIK_ECANCELLED: return "request cancelled";
+    case EIK_EQUEUE: return "device queue inconsistency";
+    case EIK_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+int eik_create(eik_ctx** out, const eik_opts* opts) {
+  if (!out) return EIK_EINVAL;
+  *out = nullptr;
+  eik_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    eik_opts_default(&o);
+  }
+  if (o.precision != EIK_FP64 && o.precision != EIK_FP32_POLISH) return EIK_EINVAL;
+  if (o.cell_n != 0 && size_index(o.cell_n) < 0) return EIK_EINVAL;
+  if (o.reserved || o.reserved2) return EIK_EINVAL;
+  if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
+  if (!(o.bucket_width > 0.0)) o.bucket_width = 1.0;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+    cudaGetLastError();
+    return EIK_ECUDA;
+  }
+  eik_ctx* c = new (std::nothrow) eik_ctx();
+  if (!c) return EIK_ENOMEM;
+  c->opts = o;
+  c->device = o.device;
+  if (cudaSetDevice(o.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return EIK_ECUDA;
+  }
+  for (int i = 0; i < 6; ++i) {
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      eik_destroy(c);
+      return EIK_ECUDA;
+    }
+  }
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qres;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &qres) != cudaSuccess ||
+      qres != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    eik_destroy(c);
+    return EIK_ECUDA;
+  }
+  c->encode = reinterpret_cast<EncodeTiledFn>(fn);
+  *out = c;
+  return EIK_OK;
+}
+
+int eik_destroy(eik_ctx* c) {
+  if (!c) return EIK_OK;
+  cudaSetDevice(c->device);
+  if (c->serve) serve_destroy(c->serve);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->arena) cudaFree(c->arena);
+  for (int i = 0; i < 3; ++i) {
+    if (c->d_tab[i]) cudaFree(c->d_tab[i]);
+    if (c->d_off[i]) cudaFree(c->d_off[i]);
+  }
+  for (int i = 0; i < 6; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+  return EIK_OK;
+}
+
+int eik_solve(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
+              const uint8_t* src_mask, const double* q, double tol, double* u_out,
+              eik_stats* stats) {
+  if (!ctx) return EIK_EINVAL;
+  return eik_run_batch(ctx, 1, dims, &h, &F, &src_mask, &q, tol, &u_out, true, ctx->stream,
+                       stats, 0);
+}
+
+int eik_solve_device(eik_ctx* ctx, const int64_t dims[3], double h, const float* F_dev,
+                     const uint8_t* src_mask_dev, const double* q_dev, double tol,
+                     double* u_out_dev, void* stream, eik_stats* stats) {
+  if (!ctx) return EIK_EINVAL;
+  return eik_run_batch(ctx, 1, dims, &h, &F_dev, &src_mask_dev, &q_dev, tol, &u_out_dev, false,
+                       reinterpret_cast<cudaStream_t>(stream), stats, 0);
+}
+
+int eik_solve_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
+                    const float* const* F, const uint8_t* const* src_mask,
+                    const double* const* q, double tol, double* const* u_out, eik_stats* stats) {
+  if (!ctx) return EIK_EINVAL;
+  return eik_run_batch(ctx, count, dims, h, F, src_mask, q, tol, u_out, true, ctx->stream, stats,
+                       0);
+}
+
+int eik_solve_batch_device(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
+                           const float* const* F_dev, const uint8_t* const* src_mask_dev,
+                           const double* const* q_dev, double tol, double* const* u_out_dev,
+                           void* stream, eik_stats* stats) {
+  if (!ctx) return EIK_EINVAL;
+  return eik_run_batch(ctx, count, dims, h, F_dev, src_mask_dev, q_dev, tol, u_out_dev, false,
+                       reinterpret_cast<cudaStream_t>(stream), stats, 0);
+}
+
+}  // extern "C"
+
+eik::ServeState*& eik_serve_slot(eik_ctx* ctx) { return ctx->serve; }

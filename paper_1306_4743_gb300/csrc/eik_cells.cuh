@@ -1,0 +1,337 @@
+// eik_cells.cuh -- the persistent cell kernel: the GPU restatement of the
+// parallel Heap-Cell Method's main loop (Alg. 1 and Alg. 3).
+//
+// A worker (one warp for n <= 8, a group of WPC warps for n = 16) repeats:
+//   1. pop a cell from the lowest non-empty Dial bucket (Alg. 3 l.6-11; the
+//      cell value is reset to +inf and its preferred directions are taken),
+//   2. stage the cell and its one-node face halo of u into shared memory with
+//      one TMA tensor box, and the cell's slowness with one bulk copy (the
+//      domain c~ = c U N(c) of Sec. 4),
+//   3. sweep the cell with the modified Locking Sweeping update of Alg. 2:
+//      preferred directions first, then the standard loop of 8 directions,
+//      until one whole sweep changes no value by more than kappa; each
+//      sweep direction advances over the planes i+j+k = C of the Detrixhe
+//      ordering (Sec. 3), whose nodes do not depend on each other,
+//   4. write the changed values back, and for each face with changed border
+//      values flag the neighbouring cell (the "currently downwind" rule of
+//      Sec. 4) with the smallest such value as its new cell value (Eq. 3)
+//      and the directions that sweep away from this cell,
+//   5. retire the cell (re-queue it if it was flagged while running) and
+//      decrement the active count after the flags (Sec. 5).
+// The kernel returns when no cell is queued or running.
+//
+// Min mode (REPLACE = false): u <- min(u, Lambda(u)), the monotone update of
+// Alg. 2.  Replace mode (REPLACE = true, the FP64 polish): u <- Lambda(u) at
+// every non-fixed node, so a value may also rise; a change counts when it
+// exceeds kappa + 2^-50 |u|.
+#pragma once
+#include "eik_device.cuh"
+
+namespace eik {
+
+// Standard loop of the 8 sweep directions.  Direction code d sweeps i
+// downward when bit 0 is set, j by bit 1, k by bit 2; this is the ordering
+// (+++), (-++), (--+), (+-+), (++-), (-+-), (---), (+--).
+static __constant__ int kStdOrder[8] = {0, 1, 3, 2, 4, 5, 7, 6};
+
+template <typename T, int N>
+struct Geo {
+  static constexpr int ES = (int)sizeof(T);
+  // TMA box width: smallest multiple of 16 bytes covering the N+2 halo row
+  static constexpr int BX = (((N + 2) * ES + 15) / 16) * 16 / ES;
+  static constexpr int BY = N + 2;
+  static constexpr int BZ = N + 2;
+  static constexpr int SY = BX;
+  static constexpr int SZ = BX * BY;
+  static constexpr int N3 = N * N * N;
+  static constexpr int NPLANES = 3 * (N - 1) + 1;
+  static constexpr int UBYTES = BX * BY * BZ * ES;
+  static constexpr int SBYTES = N3 * ES;
+  static constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+  // per-worker shared memory: u tile | s tile | change flags | mbarrier + scratch
+  static constexpr int OFF_S = align128(UBYTES);
+  static constexpr int OFF_CHG = OFF_S + align128(SBYTES);
+  static constexpr int OFF_BAR = OFF_CHG + align128(N3);
+  static constexpr int WORKER_BYTES = OFF_BAR + 128;
+  // CTA-wide: plane table | plane offsets
+  static constexpr int TAB_BYTES = align128(N3 * 2);
+  static constexpr int OFFS_BYTES = align128((NPLANES + 1) * 4);
+  static constexpr int HEAD_BYTES = TAB_BYTES + OFFS_BYTES;
+};
+
+template <int WPC>
+__device__ __forceinline__ void worker_sync(int worker) {
+  if constexpr (WPC == 1) {
+    __syncwarp();
+  } else {
+    bar_sync_named(1 + worker, WPC * 32);
+  }
+}
+template <int WPC>
+__device__ __forceinline__ bool worker_any(int worker, bool pred) {
+  if constexpr (WPC == 1) {
+    return __any_sync(0xffffffffu, pred) != 0;
+  } else {
+    return bar_red_or(1 + worker, WPC * 32, pred);
+  }
+}
+
+// One directional sweep of a staged cell.  Returns (worker-wide) whether a
+// node changed by more than the threshold.
+template <typename T, int N, int WPC, bool REPLACE>
+__device__ __forceinline__ bool sweep_cell(T* __restrict__ U, const T* __restrict__ S,
+                                           unsigned char* __restrict__ chg,
+                                           const unsigned short* __restrict__ tab,
+                                           const int* __restrict__ off, int dir, int tid,
+                                           int worker, T kappa, unsigned& n_updates) {
+  using G = Geo<T, N>;
+  constexpr int NT = WPC * 32;
+  const int fx = (dir & 1) ? N - 1 : 0;
+  const int fy = (dir & 2) ? N - 1 : 0;
+  const int fz = (dir & 4) ? N - 1 : 0;
+  bool changed = false;
+  for (int C = 0; C < G::NPLANES; ++C) {
+    const int beg = off[C], end = off[C + 1];
+    for (int e = beg + tid; e < end; e += NT) {
+      const unsigned pk = tab[e];
+      const int i = (int)(pk & 31u) ^ fx;
+      const int j = (int)((pk >> 5) & 31u) ^ fy;
+      const int k = (int)((pk >> 10) & 31u) ^ fz;
+      const int si = i + N * (j + N * k);
+      const T s = S[si];
+      if (s < tinf<T>()) {
+        const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+        const T v = U[t];
+        const T ax = fmin(U[t - 1], U[t + 1]);
+        const T ay = fmin(U[t - G::SY], U[t + G::SY]);
+        const T az = fmin(U[t - G::SZ], U[t + G::SZ]);
+        const T nv = local_solve(ax, ay, az, s);
+        ++n_updates;
+        if constexpr (!REPLACE) {
+          if (nv < v) {
+            U[t] = nv;
+            unsigned char lvl = 1;
+            if (v - nv > kappa) {
+              lvl = 3;
+              changed = true;
+            }
+            chg[si] |= lvl;
+          }
+        } else {
+          if (nv != v) {
+            U[t] = nv;
+            unsigned char lvl = 1;
+            if (fabs(nv - v) > kappa + fabs(v) * (T)8.8817841970012523e-16) {
+              lvl = 3;
+              changed = true;
+            }
+            chg[si] |= lvl;
+          }
+        }
+      }
+    }
+    worker_sync<WPC>(worker);
+  }
+  return worker_any<WPC>(worker, changed);
+}
+
+template <typename T, int N, int WPC, int WORKERS, bool REPLACE>
+__global__ void __launch_bounds__(WPC * 32 * WORKERS)
+    cells_kernel(const CellKernelParams p) {
+  using G = Geo<T, N>;
+  constexpr int NT = WPC * 32;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned short* tab = reinterpret_cast<unsigned short*>(smem);
+  int* off = reinterpret_cast<int*>(smem + G::TAB_BYTES);
+  for (int e = threadIdx.x; e < G::N3; e += blockDim.x) tab[e] = p.plane_tab[e];
+  for (int e = threadIdx.x; e <= G::NPLANES; e += blockDim.x) off[e] = p.plane_off[e];
+
+  const int worker = threadIdx.x / NT;
+  const int tid = threadIdx.x % NT;
+  const int lane = tid & 31;
+  const int wwarp = tid >> 5;
+  unsigned char* wbase = smem + G::HEAD_BYTES + worker * G::WORKER_BYTES;
+  T* U = reinterpret_cast<T*>(wbase);
+  T* S = reinterpret_cast<T*>(wbase + G::OFF_S);
+  unsigned char* chg = wbase + G::OFF_CHG;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(wbase + G::OFF_BAR);
+  int* wshared = reinterpret_cast<int*>(wbase + G::OFF_BAR + 16);  // [0]=cell [1]=dirs
+
+  if (tid == 0) mbar_init(bar, 1);
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  Control* ctl = p.ctl;
+  const CellArrays& cells = p.cells;
+  unsigned phase = 0;
+  unsigned long long n_visits = 0, n_sweeps = 0, n_pushes = 0;
+  unsigned n_updates = 0;
+  unsigned long long upd_total = 0;
+  int max_sweeps_seen = 0;
+
+  for (;;) {
+    // ---- 1. pop --------------------------------------------------------
+    int cell = -1;
+    unsigned pref = 0;
+    if (wwarp == 0) {
+      cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane);
+      if (lane == 0 && cell >= 0) {
+        atomicExch(cells.key + cell, kKeyInf);        // V^c <- +inf (Alg. 1 l.5)
+        pref = atomicExch(cells.dir + cell, 0u) & 0xffu;  // take preferred dirs
+      }
+      pref = __shfl_sync(0xffffffffu, pref, 0);
+      if constexpr (WPC > 1) {
+        if (lane == 0) {
+          wshared[0] = cell;
+          wshared[1] = (int)pref;
+        }
+      }
+    }
+    if constexpr (WPC > 1) {
+      worker_sync<WPC>(worker);
+      cell = wshared[0];
+      pref = (unsigned)wshared[1];
+      worker_sync<WPC>(worker);
+    }
+    if (cell < 0) break;
+
+    const int ii = cells.inst[cell];
+    const Instance I = p.inst[ii];
+    const int lc = cell - I.cell_base;
+    const int cx = lc % I.ncx;
+    const int cy = (lc / I.ncx) % I.ncy;
+    const int cz = lc / (I.ncx * I.ncy);
+    const T kappa = (T)I.kappa;
+
+    // ---- 2. stage cell + halo ------------------------------------------
+    fence_proxy_async_smem();
+    worker_sync<WPC>(worker);
+    if (tid == 0) {
+      fence_proxy_async_global();
+      mbar_arrive_expect_tx(bar, (unsigned)(G::UBYTES + G::SBYTES));
+      tma_load_3d(U, p.tmaps + ii, N * cx, N * cy, N * cz, bar);
+      bulk_load(S, static_cast<const T*>(I.s) + (size_t)lc * G::N3, (unsigned)G::SBYTES, bar);
+    }
+    for (int e = tid * 16; e < G::N3; e += NT * 16)
+      *reinterpret_cast<uint4*>(chg + e) = make_uint4(0, 0, 0, 0);
+    {
+      unsigned long long spins = 0;
+      while (!mbar_try_wait(bar, phase)) {
+        if (++spins > (1ull << 26)) {
+          set_status(ctl, EIK_ETIMEOUT);
+          // wait once more, bounded, for the copies in flight
+          for (unsigned long long r = 0; r < (1ull << 26) && !mbar_try_wait(bar, phase); ++r) {
+          }
+          return;
+        }
+      }
+    }
+    phase ^= 1u;
+    worker_sync<WPC>(worker);
+
+    // ---- 3. sweeps -----------------------------------------------------
+    int nsw = 0;
+    bool converged = false;
+    // preferred directions first, in the standard order
+    for (int r = 0; r < 8 && !converged; ++r) {
+      const int d = kStdOrder[r];
+      if (!((pref >> d) & 1u)) continue;
+      const bool ch = sweep_cell<T, N, WPC, REPLACE>(U, S, chg, tab, off, d, tid, worker, kappa,
+                                                     n_updates);
+      ++nsw;
+      if (!ch) converged = true;
+    }
+    // then the standard loop until a sweep changes nothing
+    for (int r = 0; !converged; r = (r + 1) & 7) {
+      if (nsw >= p.max_sweeps) break;
+      const bool ch = sweep_cell<T, N, WPC, REPLACE>(U, S, chg, tab, off, kStdOrder[r], tid,
+                                                     worker, kappa, n_updates);
+      ++nsw;
+      if (!ch) converged = true;
+    }
+    upd_total += n_updates;
+    n_updates = 0;
+    if (!converged) {
+      if constexpr (REPLACE) {
+        if (tid == 0) atomicOr(cells.state + cell, kStDirty);  // visit again later
+      } else {
+        if (tid == 0) set_status(ctl, EIK_ENOCONV);
+      }
+    }
+
+    // ---- 4. write back + flag downwind neighbours ------------------------
+    {
+      T* gu = static_cast<T*>(I.u);
+      const long long px = I.px, pxy = I.px * I.py;
+      const long long g0 = (long long)(N * cx + 1) + px * (N * cy + 1) + pxy * (N * cz + 1);
+      for (int e = tid; e < G::N3; e += NT) {
+        if (chg[e] & 1u) {
+          const int i = e % N, j = (e / N) % N, k = e / (N * N);
+          gu[g0 + i + px * j + pxy * k] = U[(i + 1) + G::SY * (j + 1) + G::SZ * (k + 1)];
+        }
+      }
+      __threadfence();
+      worker_sync<WPC>(worker);
+    }
+    for (int f = wwarp; f < 6; f += WPC) {
+      const int axis = f >> 1, upper = f & 1;
+      const int ncoord = (axis == 0 ? cx : axis == 1 ? cy : cz) + (upper ? 1 : -1);
+      const int nlim = axis == 0 ? I.ncx : axis == 1 ? I.ncy : I.ncz;
+      if (ncoord < 0 || ncoord >= nlim) continue;  // warp-uniform
+      unsigned m = 0xffffffffu;
+      for (int q = lane; q < N * N; q += 32) {
+        const int a = q % N, b = q / N;
+        int i, j, k;
+        if (axis == 0) { i = upper ? N - 1 : 0; j = a; k = b; }
+        else if (axis == 1) { i = a; j = upper ? N - 1 : 0; k = b; }
+        else { i = a; j = b; k = upper ? N - 1 : 0; }
+        if (chg[i + N * (j + N * k)] & 2u) {
+          const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+          const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
+          const T vi = U[t];
+          const T vj = U[upper ? t + step : t - step];  // halo value
+          if (REPLACE || vi < vj) {
+            const unsigned kk = key_of(vi);
+            m = kk < m ? kk : m;
+          }
+        }
+      }
+      m = __reduce_min_sync(0xffffffffu, m);
+      if (lane == 0 && m != 0xffffffffu) {
+        const int ncx2 = axis == 0 ? ncoord : cx;
+        const int ncy2 = axis == 1 ? ncoord : cy;
+        const int ncz2 = axis == 2 ? ncoord : cz;
+        const unsigned nb =
+            (unsigned)(I.cell_base + ncx2 + I.ncx * (ncy2 + I.ncy * ncz2));
+        // directions that sweep away from this cell into the neighbour
+        const unsigned bit = 1u << axis;
+        unsigned dirs = 0;
+        for (int d = 0; d < 8; ++d)
+          if (((d & bit) != 0) == (upper == 0)) dirs |= 1u << d;
+        __threadfence();
+        flag_cell(cells, ctl, nb, m, dirs, &n_pushes);
+      }
+    }
+    worker_sync<WPC>(worker);
+
+    // ---- 5. retire -------------------------------------------------------
+    if (tid == 0) {
+      retire_cell(cells, ctl, (unsigned)cell, &n_pushes);
+      ++n_visits;
+      n_sweeps += (unsigned long long)nsw;
+      if (nsw > max_sweeps_seen) max_sweeps_seen = nsw;
+    }
+  }
+
+  // counters
+  unsigned long long* cnt = ctl->counters[p.pass];
+  if (upd_total) atomicAdd(cnt + kCntUpdates, upd_total);
+  if (tid == 0) {
+    if (n_visits) atomicAdd(cnt + kCntVisits, n_visits);
+    if (n_sweeps) atomicAdd(cnt + kCntSweeps, n_sweeps);
+    if (max_sweeps_seen) atomicMax(cnt + kCntMaxSweeps, (unsigned long long)max_sweeps_seen);
+  }
+  if (n_pushes) atomicAdd(cnt + kCntPushes, n_pushes);
+}
+
+}  // namespace eik

@@ -1,0 +1,51 @@
+// eik_cells_launch.cuh -- launch configuration of the persistent cell kernel
+// per (value type, cell size): workers of one warp for n <= 8, of four warps
+// for n = 16; grid = SM count x resident CTAs per SM (all CTAs co-resident,
+// as a persistent kernel needs).
+#pragma once
+#include "eik_cells.cuh"
+#include "eik_prep.h"
+
+namespace eik {
+
+template <int N>
+struct WorkerShape;
+template <>
+struct WorkerShape<4> { static constexpr int WPC = 1, WORKERS = 8; };
+template <>
+struct WorkerShape<8> { static constexpr int WPC = 1, WORKERS = 4; };
+template <>
+struct WorkerShape<16> { static constexpr int WPC = 4, WORKERS = 1; };
+
+template <typename T, int N>
+constexpr int cells_smem_bytes() {
+  using G = Geo<T, N>;
+  return G::HEAD_BYTES + WorkerShape<N>::WORKERS * G::WORKER_BYTES;
+}
+
+template <typename T, int N, bool REPLACE>
+cudaError_t launch_cells_t(const CellKernelParams& p, int sms, cudaStream_t st, int* grid_out) {
+  constexpr int WPC = WorkerShape<N>::WPC, WORKERS = WorkerShape<N>::WORKERS;
+  constexpr int threads = WPC * 32 * WORKERS;
+  constexpr int smem = cells_smem_bytes<T, N>();
+  auto kern = cells_kernel<T, N, WPC, WORKERS, REPLACE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = sms * per_sm;
+  if (grid_out) *grid_out = grid;
+  kern<<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+void shape_t(int* threads, int* smem, int* workers) {
+  *threads = WorkerShape<N>::WPC * 32 * WorkerShape<N>::WORKERS;
+  *smem = cells_smem_bytes<T, N>();
+  *workers = WorkerShape<N>::WORKERS;
+}
+
+}  // namespace eik

@@ -1,0 +1,64 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry
+point that include/eik.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "eik.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eik_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("eik_create", "eik_solve", "eik_destroy", "eik_submit", "eik_poll",
+                     "eik_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1306_4743_gb300 import eik
+    lib = eik.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(eik.EXPORTED) == declared_functions()
+
+
+def test_defaults_and_strerror_without_gpu():
+    from paper_1306_4743_gb300 import eik
+    o = eik.default_opts()
+    assert o.precision == 1 and o.cell_n == 0 and o.spin_cap_us == 5_000_000
+    assert o.max_sweeps_per_visit == 4096 and o.bucket_width == 1.0
+    lib = eik.load()
+    assert lib.eik_strerror(0) == b"ok"
+    assert lib.eik_strerror(5).startswith(b"device wait")
+    assert lib.eik_strerror(12345) == b"unknown status"
+
+
+def test_create_fails_cleanly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1306_4743_gb300 import eik
+    with pytest.raises(eik.EikError) as e:
+        eik.Solver()
+    assert e.value.status == 4  # EIK_ECUDA, not a crash
+
+
+def test_invalid_options_rejected_before_device_use():
+    from paper_1306_4743_gb300 import eik
+    lib = eik.load()
+    o = eik.default_opts()
+    o.cell_n = 5
+    ctx = ctypes.c_void_p()
+    assert lib.eik_create(ctypes.byref(ctx), ctypes.byref(o)) == 1
+    o = eik.default_opts()
+    o.precision = 7
+    assert lib.eik_create(ctypes.byref(ctx), ctypes.byref(o)) == 1
+    assert not ctx

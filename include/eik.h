@@ -72,16 +72,28 @@ typedef struct {
   int device;               /* CUDA device ordinal (default 0) */
   int precision;            /* eik_precision (default EIK_FP32_POLISH) */
   int cell_n;               /* nodes per cell side: 4, 8 or 16; 0 = choose by
-                               the built-in size table (default 0) */
-  int reserved;             /* must be 0 */
+                               grid size: 16 from 2^21 nodes up, else 8
+                               (default 0) */
+  int max_ctas;             /* CTAs of the persistent cell kernel; 0 = every
+                               CTA that fits on the device at once (default) */
   size_t hbm_budget_bytes;  /* device-memory limit of this context; 0 = none */
   uint64_t spin_cap_us;     /* longest device wait without global progress,
                                in microseconds (default 5,000,000); 0 makes
                                every idle wait fail at once (test hook) */
   double bucket_width;      /* width of one queue bucket in units of
-                               (cell edge x mean slowness); <= 0 = default 1 */
+                               (cell edge x mean slowness); <= 0 = default 0.5 */
   int max_sweeps_per_visit; /* sweep limit of one cell visit (default 4096) */
-  int reserved2;            /* must be 0 */
+  int queue_order;          /* 0 = strict: the next bucket starts once every
+                               cell of the current one is finished;
+                               1 = relaxed: once the current bucket is empty
+                               (default) */
+  double bulk_kappa_rel;    /* EIK_FP32_POLISH only: change threshold of the
+                               FP32 bulk sweeps, in units of (cell edge x mean
+                               slowness) (default 3e-5).  Stopping the bulk
+                               early leaves values high, never low, and the
+                               FP64 polish starts above the fixed point, so
+                               this trades bulk sweeps for polish sweeps and
+                               does not change the result. */
 } eik_opts;
 
 /* Counters and results of one solve (of the whole batch for batch calls). */
@@ -104,6 +116,15 @@ typedef struct {
   double u_max;                 /* largest finite u */
   double seconds_bulk;          /* device time of the bulk cell kernel */
   double seconds_polish;        /* device time of the polish cell kernel */
+  uint64_t kernel_launches;     /* CUDA kernels this call launched */
+  int grid_ctas;                /* CTAs of the persistent cell kernel */
+  int fallback_used;            /* 1 if the replace-mode polish ran */
+  double busy_seconds_bulk;     /* sum over cell visits of their duration */
+  double busy_seconds_polish;
+  uint64_t fallback_visits;
+  double phase_seconds[2][4];   /* [bulk, polish] x [waiting in the queue pop,
+                                   TMA staging, sweeps, write-back + flags + retire],
+                                   summed over workers */
 } eik_stats;
 
 /* Default options. */

@@ -111,7 +111,8 @@ struct LaunchPlan {
   std::vector<InstPlan> inst;
   int total_cells = 0, max_cells = 0;
   long long max_padded_b = 0, max_padded64 = 0, max_cellnodes = 0, max_nodes = 0;
-  size_t off_key, off_state, off_dir, off_inst, off_next, off_heads, off_ctl, off_nsrc;
+  size_t off_key, off_state, off_dir, off_inst, off_next, off_deps, off_down, off_heads, off_ctl,
+      off_nsrc;
   size_t off_inst_b, off_inst64, off_tmap_b, off_tmap64, off_prep, off_pol, off_fin;
   size_t total = 0;
   size_t small_begin = 0, small_end = 0;  // tables copied from the host in one go
@@ -129,7 +130,9 @@ int choose_cell_n(eik_ctx* ctx, long long nodes) {
   while ((1ll << (lg + 1)) <= nodes) ++lg;
   auto it = ctx->tuned.find(lg);
   if (it != ctx->tuned.end()) return it->second;
-  return 8;
+  // built-in size table: 16^3 cells from ~128^3 nodes up (fewer, longer
+  // visits keep the queue latency small against the sweeping), else 8^3
+  return nodes >= (1ll << 21) ? 16 : 8;
 }
 
 void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, int n, bool polish,
@@ -188,7 +191,9 @@ void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, i
   L.off_dir = take(cur, (size_t)cells * 4);
   L.off_inst = take(cur, (size_t)cells * 4);
   L.off_next = take(cur, (size_t)cells * 4);
-  L.off_heads = take(cur, (size_t)kNumBuckets * 8);
+  L.off_deps = take(cur, (size_t)cells * 4);
+  L.off_down = take(cur, (size_t)cells * 4);
+  L.off_heads = take(cur, (size_t)kNumBuckets * 12);  // heads, then run counts
   // small tables, filled on the host and copied in one transfer
   L.small_begin = align_up(cur, 256);
   L.off_ctl = take(cur, sizeof(Control));
@@ -388,6 +393,8 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
     Q.ncells = I.ncells;
     Q.n = n;
     FinalInstance& Fi = hfin[t];
+    Fi.mask = P.mask;
+    Fi.q = P.q;
     Fi.u64 = A + I.off_u64;
     Fi.s64 = A + I.off_s64;
     Fi.out = host_io ? reinterpret_cast<double*>(A + I.off_out) : u_out[t];
@@ -414,7 +421,7 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   }
   CK(cudaMemcpyAsync(A + L.small_begin, hs, L.small_end - L.small_begin, cudaMemcpyHostToDevice,
                      st));
-  CK(cudaMemsetAsync(A + L.off_heads, 0, (size_t)kNumBuckets * 8, st));
+  CK(cudaMemsetAsync(A + L.off_heads, 0, (size_t)kNumBuckets * 12, st));
 
   CellArrays cells;
   cells.key = reinterpret_cast<unsigned*>(A + L.off_key);
@@ -423,13 +430,17 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   cells.inst = reinterpret_cast<int*>(A + L.off_inst);
   cells.next = reinterpret_cast<unsigned*>(A + L.off_next);
   cells.heads = reinterpret_cast<unsigned long long*>(A + L.off_heads);
+  cells.run = reinterpret_cast<int*>(A + L.off_heads + (size_t)kNumBuckets * 8);
+  cells.deps = reinterpret_cast<int*>(A + L.off_deps);
+  cells.down = reinterpret_cast<unsigned*>(A + L.off_down);
   Control* dctl = reinterpret_cast<Control*>(A + L.off_ctl);
 
   CK(cudaEventRecord(ctx->ev[0], st));
-  double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 1.0;
+  double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 0.5;
   CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), count,
-                      L.max_padded_b, L.max_cellnodes, L.max_cells, L.total_cells, cells, dctl,
-                      reinterpret_cast<int*>(A + L.off_nsrc), !polish, n, wf, ctx->sms, st));
+                      L.max_padded_b, L.max_cellnodes, L.max_nodes, L.max_cells, L.total_cells,
+                      cells, dctl, reinterpret_cast<int*>(A + L.off_nsrc), !polish, n, wf,
+                      ctx->opts.bulk_kappa_rel, ctx->sms, st));
 
   CellKernelParams p;
   p.inst = reinterpret_cast<const Instance*>(A + L.off_inst_b);
@@ -441,18 +452,36 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   p.spin_cap_ns = ctx->opts.spin_cap_us * 1000ull;
   p.max_sweeps = ctx->opts.max_sweeps_per_visit;
   p.pass = 0;
+  p.max_ctas = ctx->opts.max_ctas;
+  p.kappa_from_ctl = polish ? 1 : 0;
+  p.relaxed = ctx->opts.queue_order;
+  p.gated = 0;
   CK(cudaEventRecord(ctx->ev[1], st));
-  CK(launch_cells(!polish, false, n, p, ctx->sms, st, nullptr));
+  int grid_ctas = 0;
+  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas));
   CK(cudaEventRecord(ctx->ev[2], st));
   if (polish) {
     CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), count,
-                          L.max_padded64, L.max_cells, L.total_cells, cells, dctl, ctx->sms, st));
+                          L.max_padded64, L.max_nodes, L.max_cells, L.total_cells, cells, dctl,
+                          ctx->sms, st));
     p.inst = reinterpret_cast<const Instance*>(A + L.off_inst64);
     p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap64);
     p.pass = 1;
+    p.kappa_from_ctl = 0;
+    p.gated = 1;
     CK(cudaEventRecord(ctx->ev[3], st));
-    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
+    // monotone FP64 sweeps down from the lifted FP32 result
+    CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr));
     CK(cudaEventRecord(ctx->ev[4], st));
+    // fallback, gated on the device: if some u ended below the fixed point
+    // (lift too small), polish again with replace-mode sweeps
+    CK(launch_fallback_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol),
+                            reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
+                            L.max_nodes, L.max_cells, L.total_cells, cells, dctl, tol, ctx->sms,
+                            st));
+    p.pass = 2;
+    p.gated = 0;
+    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
   }
   CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
                              L.max_nodes, dctl, ctx->sms, st));
@@ -482,22 +511,41 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
     stats->cell_visits = hres->counters[0][kCntVisits];
     stats->sweeps = hres->counters[0][kCntSweeps];
     stats->node_updates = hres->counters[0][kCntUpdates];
-    stats->polish_visits = hres->counters[1][kCntVisits];
-    stats->polish_sweeps = hres->counters[1][kCntSweeps];
-    stats->polish_node_updates = hres->counters[1][kCntUpdates];
-    stats->queue_pushes = hres->counters[0][kCntPushes] + hres->counters[1][kCntPushes];
+    stats->polish_visits = hres->counters[1][kCntVisits] + hres->counters[2][kCntVisits];
+    stats->polish_sweeps = hres->counters[1][kCntSweeps] + hres->counters[2][kCntSweeps];
+    stats->polish_node_updates = hres->counters[1][kCntUpdates] + hres->counters[2][kCntUpdates];
+    stats->queue_pushes = hres->counters[0][kCntPushes] + hres->counters[1][kCntPushes] +
+                          hres->counters[2][kCntPushes];
     stats->nonfinite = hres->nonfinite;
     stats->nodes = (uint64_t)nodes_total;
     stats->cell_n_used = n;
+    // reset, init u, init s, setup, seed, cells [, convert, keys, setup,
+    // seed, cells], residual + copy-out
+    stats->kernel_launches = polish ? 20 : 8;
+    stats->grid_ctas = grid_ctas;
+    stats->fallback_used = hres->counters[2][kCntPushes] > 0;
+    stats->fallback_visits = hres->counters[2][kCntVisits];
+    stats->busy_seconds_bulk = hres->counters[0][kCntBusyNs] * 1e-9;
+    stats->busy_seconds_polish = hres->counters[1][kCntBusyNs] * 1e-9;
+    for (int ps = 0; ps < 2; ++ps) {
+      stats->phase_seconds[ps][0] = hres->counters[ps][kCntPopNs] * 1e-9;
+      stats->phase_seconds[ps][1] = hres->counters[ps][kCntStageNs] * 1e-9;
+      stats->phase_seconds[ps][2] = hres->counters[ps][kCntSweepNs] * 1e-9;
+      stats->phase_seconds[ps][3] = hres->counters[ps][kCntFlagNs] * 1e-9;
+    }
     stats->precision_used = polish ? EIK_FP32_POLISH : EIK_FP64;
     double r;
     unsigned long long rb = hres->resid_bits;
     memcpy(&r, &rb, 8);
     stats->residual_max = r;
-    unsigned long long ub = hres->umax_bits;
+    unsigned long long ub = hres->final_umax_bits;
     ub = (ub & 0x8000000000000000ull) ? (ub & 0x7fffffffffffffffull) : ~ub;
     memcpy(&r, &ub, 8);
-    stats->u_max = hres->umax_bits ? r : 0.0;
+    double qb;
+    unsigned long long qo = hres->min_q_ord;
+    qo = (qo & 0x8000000000000000ull) ? (qo & 0x7fffffffffffffffull) : ~qo;
+    memcpy(&qb, &qo, 8);
+    stats->u_max = hres->final_umax_bits ? r + qb : 0.0;
   }
   if (hres->status) return hres->status;
   if (hres->nonfinite) return EIK_ENOCONV;
@@ -516,8 +564,10 @@ int eik_opts_default(eik_opts* o) {
   o->cell_n = 0;
   o->hbm_budget_bytes = 0;
   o->spin_cap_us = 5000000ull;
-  o->bucket_width = 1.0;
+  o->bucket_width = 0.5;
   o->max_sweeps_per_visit = 4096;
+  o->bulk_kappa_rel = 3.0e-5;
+  o->queue_order = 1;
   return EIK_OK;
 }
 
@@ -548,9 +598,10 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
   }
   if (o.precision != EIK_FP64 && o.precision != EIK_FP32_POLISH) return EIK_EINVAL;
   if (o.cell_n != 0 && size_index(o.cell_n) < 0) return EIK_EINVAL;
-  if (o.reserved || o.reserved2) return EIK_EINVAL;
+  if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1) return EIK_EINVAL;
   if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
-  if (!(o.bucket_width > 0.0)) o.bucket_width = 1.0;
+  if (!(o.bulk_kappa_rel >= 0.0) || isinf(o.bulk_kappa_rel)) return EIK_EINVAL;
+  if (!(o.bucket_width > 0.0)) o.bucket_width = 0.5;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
     cudaGetLastError();

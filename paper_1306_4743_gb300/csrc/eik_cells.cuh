@@ -34,6 +34,10 @@ namespace eik {
 // (+++), (-++), (--+), (+-+), (++-), (-+-), (---), (+--).
 static __constant__ int kStdOrder[8] = {0, 1, 3, 2, 4, 5, 7, 6};
 
+// Per-node bits of the staged cell: written back, changed by more than
+// kappa (flags the neighbour cell), active (to be recomputed, Alg. 2).
+constexpr unsigned char kWritten = 1, kBig = 2, kActive = 4;
+
 template <typename T, int N>
 struct Geo {
   static constexpr int ES = (int)sizeof(T);
@@ -92,42 +96,58 @@ __device__ __forceinline__ bool sweep_cell(T* __restrict__ U, const T* __restric
   bool changed = false;
   for (int C = 0; C < G::NPLANES; ++C) {
     const int beg = off[C], end = off[C + 1];
-    for (int e = beg + tid; e < end; e += NT) {
-      const unsigned pk = tab[e];
-      const int i = (int)(pk & 31u) ^ fx;
-      const int j = (int)((pk >> 5) & 31u) ^ fy;
-      const int k = (int)((pk >> 10) & 31u) ^ fz;
-      const int si = i + N * (j + N * k);
-      const T s = S[si];
-      if (s < tinf<T>()) {
-        const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
-        const T v = U[t];
-        const T ax = fmin(U[t - 1], U[t + 1]);
-        const T ay = fmin(U[t - G::SY], U[t + G::SY]);
-        const T az = fmin(U[t - G::SZ], U[t + G::SZ]);
-        const T nv = local_solve(ax, ay, az, s);
-        ++n_updates;
-        if constexpr (!REPLACE) {
-          if (nv < v) {
-            U[t] = nv;
-            unsigned char lvl = 1;
-            if (v - nv > kappa) {
-              lvl = 3;
-              changed = true;
+    // Nodes of one plane do not depend on each other: each thread takes two
+    // per pass, so their loads and arithmetic overlap.
+    for (int e0 = beg + tid; e0 < end; e0 += 2 * NT) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = e0 + h * NT;
+        if (e >= end) break;
+        const unsigned pk = tab[e];
+        const int i = (int)(pk & 31u) ^ fx;
+        const int j = (int)((pk >> 5) & 31u) ^ fy;
+        const int k = (int)((pk >> 10) & 31u) ^ fz;
+        const int si = i + N * (j + N * k);
+        const unsigned char c0 = chg[si];
+        if (!(c0 & kActive)) continue;  // Alg. 2 l.1-2: inactive, nothing to do
+        const T s = S[si];
+        unsigned char c1 = c0 & (unsigned char)~kActive;  // Alg. 2 l.4
+        if (s < tinf<T>()) {
+          const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+          const T v = U[t];
+          const T xm = U[t - 1], xp = U[t + 1];
+          const T ym = U[t - G::SY], yp = U[t + G::SY];
+          const T zm = U[t - G::SZ], zp = U[t + G::SZ];
+          const T nv = local_solve(nmin(xm, xp), nmin(ym, yp), nmin(zm, zp), s);
+          ++n_updates;
+          bool big;
+          if constexpr (!REPLACE) {
+            big = nv < v && v - nv > kappa;
+            if (nv < v) {
+              U[t] = nv;
+              c1 |= big ? 3 : 1;
             }
-            chg[si] |= lvl;
+          } else {
+            big = nv != v && fabs(nv - v) > kappa + fabs(v) * (T)8.8817841970012523e-16;
+            if (nv != v) {
+              U[t] = nv;
+              c1 |= big ? 3 : 1;
+            }
           }
-        } else {
-          if (nv != v) {
-            U[t] = nv;
-            unsigned char lvl = 1;
-            if (fabs(nv - v) > kappa + fabs(v) * (T)8.8817841970012523e-16) {
-              lvl = 3;
-              changed = true;
-            }
-            chg[si] |= lvl;
+          if (big) {
+            changed = true;
+            // Alg. 2 l.8-10: neighbours (in this cell) that may now use the
+            // new value become active; neighbours in other cells are reached
+            // through the face flags.
+            if (i > 0 && (REPLACE || xm > nv)) chg[si - 1] |= kActive;
+            if (i < N - 1 && (REPLACE || xp > nv)) chg[si + 1] |= kActive;
+            if (j > 0 && (REPLACE || ym > nv)) chg[si - N] |= kActive;
+            if (j < N - 1 && (REPLACE || yp > nv)) chg[si + N] |= kActive;
+            if (k > 0 && (REPLACE || zm > nv)) chg[si - N * N] |= kActive;
+            if (k < N - 1 && (REPLACE || zp > nv)) chg[si + N * N] |= kActive;
           }
         }
+        chg[si] = c1;
       }
     }
     worker_sync<WPC>(worker);
@@ -164,7 +184,9 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   Control* ctl = p.ctl;
   const CellArrays& cells = p.cells;
   unsigned phase = 0;
-  unsigned long long n_visits = 0, n_sweeps = 0, n_pushes = 0;
+  unsigned slot = 0;  // ring slot of the bucket the current cell came from
+  unsigned long long n_visits = 0, n_sweeps = 0, n_pushes = 0, busy_ns = 0;
+  unsigned long long pop_ns = 0, stage_ns = 0, sweep_ns = 0, flag_ns = 0;
   unsigned n_updates = 0;
   unsigned long long upd_total = 0;
   int max_sweeps_seen = 0;
@@ -173,8 +195,10 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     // ---- 1. pop --------------------------------------------------------
     int cell = -1;
     unsigned pref = 0;
+    unsigned long long t_pop0 = 0;
+    if (tid == 0) t_pop0 = global_timer_ns();
     if (wwarp == 0) {
-      cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane);
+      cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane, &slot, p.relaxed != 0);
       if (lane == 0 && cell >= 0) {
         atomicExch(cells.key + cell, kKeyInf);        // V^c <- +inf (Alg. 1 l.5)
         pref = atomicExch(cells.dir + cell, 0u) & 0xffu;  // take preferred dirs
@@ -194,6 +218,11 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       worker_sync<WPC>(worker);
     }
     if (cell < 0) break;
+    unsigned long long t_pop = 0;
+    if (tid == 0) {
+      t_pop = global_timer_ns();
+      pop_ns += t_pop - t_pop0;
+    }
 
     const int ii = cells.inst[cell];
     const Instance I = p.inst[ii];
@@ -201,7 +230,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     const int cx = lc % I.ncx;
     const int cy = (lc / I.ncx) % I.ncy;
     const int cz = lc / (I.ncx * I.ncy);
-    const T kappa = (T)I.kappa;
+    const T kappa = (T)(p.kappa_from_ctl ? ctl->kappa_bulk : I.kappa);
 
     // ---- 2. stage cell + halo ------------------------------------------
     fence_proxy_async_smem();
@@ -212,8 +241,10 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       tma_load_3d(U, p.tmaps + ii, N * cx, N * cy, N * cz, bar);
       bulk_load(S, static_cast<const T*>(I.s) + (size_t)lc * G::N3, (unsigned)G::SBYTES, bar);
     }
+    // every node starts active: the halo may have changed since the last visit
     for (int e = tid * 16; e < G::N3; e += NT * 16)
-      *reinterpret_cast<uint4*>(chg + e) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(chg + e) = make_uint4(0x04040404u, 0x04040404u, 0x04040404u,
+                                                      0x04040404u);
     {
       unsigned long long spins = 0;
       while (!mbar_try_wait(bar, phase)) {
@@ -228,6 +259,11 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     }
     phase ^= 1u;
     worker_sync<WPC>(worker);
+    unsigned long long t_sw = 0;
+    if (tid == 0) {
+      t_sw = global_timer_ns();
+      stage_ns += t_sw - t_pop;
+    }
 
     // ---- 3. sweeps -----------------------------------------------------
     int nsw = 0;
@@ -259,65 +295,105 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       }
     }
 
-    // ---- 4. write back + flag downwind neighbours ------------------------
-    {
-      T* gu = static_cast<T*>(I.u);
-      const long long px = I.px, pxy = I.px * I.py;
-      const long long g0 = (long long)(N * cx + 1) + px * (N * cy + 1) + pxy * (N * cz + 1);
-      for (int e = tid; e < G::N3; e += NT) {
-        if (chg[e] & 1u) {
-          const int i = e % N, j = (e / N) % N, k = e / (N * N);
-          gu[g0 + i + px * j + pxy * k] = U[(i + 1) + G::SY * (j + 1) + G::SZ * (k + 1)];
-        }
-      }
-      __threadfence();
-      worker_sync<WPC>(worker);
+    unsigned long long t_fl = 0;
+    if (tid == 0) {
+      t_fl = global_timer_ns();
+      sweep_ns += t_fl - t_sw;
     }
+    // ---- 4. flag keys, write back, flag downwind neighbours -------------
+    T* gu = static_cast<T*>(I.u);
+    const long long px = I.px, pxy = I.px * I.py;
+    const long long g0 = (long long)(N * cx + 1) + px * (N * cy + 1) + pxy * (N * cz + 1);
+    unsigned* fkey = reinterpret_cast<unsigned*>(wshared + 2);  // [6]
     for (int f = wwarp; f < 6; f += WPC) {
       const int axis = f >> 1, upper = f & 1;
       const int ncoord = (axis == 0 ? cx : axis == 1 ? cy : cz) + (upper ? 1 : -1);
       const int nlim = axis == 0 ? I.ncx : axis == 1 ? I.ncy : I.ncz;
-      if (ncoord < 0 || ncoord >= nlim) continue;  // warp-uniform
       unsigned m = 0xffffffffu;
-      for (int q = lane; q < N * N; q += 32) {
-        const int a = q % N, b = q / N;
-        int i, j, k;
-        if (axis == 0) { i = upper ? N - 1 : 0; j = a; k = b; }
-        else if (axis == 1) { i = a; j = upper ? N - 1 : 0; k = b; }
-        else { i = a; j = b; k = upper ? N - 1 : 0; }
-        if (chg[i + N * (j + N * k)] & 2u) {
-          const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
-          const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
-          const T vi = U[t];
-          const T vj = U[upper ? t + step : t - step];  // halo value
-          if (REPLACE || vi < vj) {
-            const unsigned kk = key_of(vi);
-            m = kk < m ? kk : m;
+      if (ncoord >= 0 && ncoord < nlim) {  // warp-uniform
+        for (int q = lane; q < N * N; q += 32) {
+          const int a = q % N, b = q / N;
+          int i, j, k;
+          if (axis == 0) { i = upper ? N - 1 : 0; j = a; k = b; }
+          else if (axis == 1) { i = a; j = upper ? N - 1 : 0; k = b; }
+          else { i = a; j = b; k = upper ? N - 1 : 0; }
+          if (chg[i + N * (j + N * k)] & 2u) {
+            const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+            const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
+            const T vi = U[t];
+            const T vj = U[upper ? t + step : t - step];  // halo value
+            // Min mode: only a border value below its neighbour's can be
+            // used by the neighbour, and the (possibly stale) halo value is
+            // never below the neighbour's current one, so this test misses
+            // no inflow.  Replace mode: values may also rise, so every
+            // change is passed on.
+            if (REPLACE || vi < vj) {
+              const unsigned kk = key_of(vi);
+              m = kk < m ? kk : m;
+            }
           }
         }
+        m = __reduce_min_sync(0xffffffffu, m);
       }
-      m = __reduce_min_sync(0xffffffffu, m);
-      if (lane == 0 && m != 0xffffffffu) {
+      if (lane == 0) fkey[f] = m;
+    }
+    worker_sync<WPC>(worker);
+    for (int e = tid; e < G::N3; e += NT) {
+      if (chg[e] & 1u) {
+        const int i = e % N, j = (e / N) % N, k = e / (N * N);
+        gu[g0 + i + px * j + pxy * k] = U[(i + 1) + G::SY * (j + 1) + G::SZ * (k + 1)];
+      }
+    }
+    __threadfence();
+    worker_sync<WPC>(worker);
+    if (wwarp == 0 && lane < 6) {
+      // one lane per face: the six flag sequences run concurrently
+      __threadfence();
+      const int f = lane;
+      const unsigned m = fkey[f];
+      if (m != 0xffffffffu) {
+        const int axis = f >> 1, upper = f & 1;
+        const int ncoord = (axis == 0 ? cx : axis == 1 ? cy : cz) + (upper ? 1 : -1);
         const int ncx2 = axis == 0 ? ncoord : cx;
         const int ncy2 = axis == 1 ? ncoord : cy;
         const int ncz2 = axis == 2 ? ncoord : cz;
-        const unsigned nb =
-            (unsigned)(I.cell_base + ncx2 + I.ncx * (ncy2 + I.ncy * ncz2));
+        const unsigned nb = (unsigned)(I.cell_base + ncx2 + I.ncx * (ncy2 + I.ncy * ncz2));
         // directions that sweep away from this cell into the neighbour
         const unsigned bit = 1u << axis;
         unsigned dirs = 0;
         for (int d = 0; d < 8; ++d)
           if (((d & bit) != 0) == (upper == 0)) dirs |= 1u << d;
-        __threadfence();
-        flag_cell(cells, ctl, nb, m, dirs, &n_pushes);
+        flag_cell(cells, ctl, nb, m, dirs, &n_pushes, p.gated != 0);
+      }
+      if (p.gated) {
+        // first visit done: release downwind neighbours whose last upwind
+        // dependency this was
+        const unsigned dn = (lane == 0) ? atomicOr(cells.down + cell, 0x100u) : 0u;
+        const unsigned dl = __shfl_sync(0x3fu, dn, 0);
+        if (!(dl & 0x100u) && ((dl >> f) & 1u)) {
+          const int axis = f >> 1, upper = f & 1;
+          const int ncoord = (axis == 0 ? cx : axis == 1 ? cy : cz) + (upper ? 1 : -1);
+          const int ncx2 = axis == 0 ? ncoord : cx;
+          const int ncy2 = axis == 1 ? ncoord : cy;
+          const int ncz2 = axis == 2 ? ncoord : cz;
+          const unsigned nb = (unsigned)(I.cell_base + ncx2 + I.ncx * (ncy2 + I.ncy * ncz2));
+          if (atomicSub(cells.deps + nb, 1) == 1) {
+            const unsigned kb = ld_relaxed_u32(cells.key + nb);
+            flag_cell(cells, ctl, nb, kb, 0u, &n_pushes, false);
+          }
+        }
       }
     }
-    worker_sync<WPC>(worker);
+    if (wwarp == 0) __syncwarp();
+    if (tid == 0) flag_ns += global_timer_ns() - t_fl;
 
     // ---- 5. retire -------------------------------------------------------
     if (tid == 0) {
-      retire_cell(cells, ctl, (unsigned)cell, &n_pushes);
+      retire_cell(cells, ctl, (unsigned)cell, slot, &n_pushes);
+      busy_ns += global_timer_ns() - t_pop;
       ++n_visits;
+      // the watchdog only needs to see that visits complete: publish every 8th
+      if ((n_visits & 7u) == 1u) atomicAdd(&ctl->progress, 8u);
       n_sweeps += (unsigned long long)nsw;
       if (nsw > max_sweeps_seen) max_sweeps_seen = nsw;
     }
@@ -330,6 +406,11 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     if (n_visits) atomicAdd(cnt + kCntVisits, n_visits);
     if (n_sweeps) atomicAdd(cnt + kCntSweeps, n_sweeps);
     if (max_sweeps_seen) atomicMax(cnt + kCntMaxSweeps, (unsigned long long)max_sweeps_seen);
+    if (busy_ns) atomicAdd(cnt + kCntBusyNs, busy_ns);
+    atomicAdd(cnt + kCntPopNs, pop_ns);
+    atomicAdd(cnt + kCntStageNs, stage_ns);
+    atomicAdd(cnt + kCntSweepNs, sweep_ns);
+    atomicAdd(cnt + kCntFlagNs, flag_ns);
   }
   if (n_pushes) atomicAdd(cnt + kCntPushes, n_pushes);
 }

@@ -35,7 +35,14 @@ cudaError_t launch_cells_t(const CellKernelParams& p, int sms, cudaStream_t st, 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int grid = sms * per_sm;
+  int grid = sms * per_sm;
+  if (p.max_ctas > 0) {
+    if (p.max_ctas < grid) grid = p.max_ctas;
+  } else if (per_sm > 2) {
+    // Enough workers for the cells of a few buckets; more only add waiting
+    // workers whose polling slows the queue atomics of the working ones.
+    grid = sms * 2;
+  }
   if (grid_out) *grid_out = grid;
   kern<<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();

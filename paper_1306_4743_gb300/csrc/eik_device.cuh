@@ -159,6 +159,14 @@ __device__ __forceinline__ void set_status(Control* ctl, int code) {
 // FP32 variant: a discriminant below 2^-10 * 3s^2 in the 3-term branch is
 // recomputed in FP64 (the near-cancellation guard; it cannot fire except
 // through rounding of the inputs).
+// Square root on the special-function unit (about 2 ulp): the FP32 bulk
+// pass only has to land close to the fixed point; the FP64 polish settles it.
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ float local_solve(float ax, float ay, float az, float s) {
   const float lo = fminf(ax, ay), hi = fmaxf(ax, ay);
   const float a1 = fminf(lo, az), mid = fmaxf(lo, az);
@@ -167,7 +175,7 @@ __device__ __forceinline__ float local_solve(float ax, float ay, float az, float
   if (u1 <= a2) return u1;  // also covers a1 = +inf (returns +inf)
   const float s2 = s * s;
   const float b = a2 - a1;
-  const float u2 = a1 + 0.5f * (b + sqrtf(fmaxf(2.0f * s2 - b * b, 0.0f)));
+  const float u2 = a1 + 0.5f * (b + sqrt_fast(fmaxf(2.0f * s2 - b * b, 0.0f)));
   if (u2 <= a3) return u2;
   const float b3 = a3 - a1, e = b3 - b;
   float d3 = 3.0f * s2 - (b * b + b3 * b3 + e * e);
@@ -177,23 +185,78 @@ __device__ __forceinline__ float local_solve(float ax, float ay, float az, float
     const double dd = 3.0 * sd * sd - (bd * bd + b3d * b3d + ed * ed);
     return a1 + (float)((bd + b3d + sqrt(fmax(dd, 0.0))) / 3.0);
   }
-  return a1 + (b + b3 + sqrtf(d3)) * (1.0f / 3.0f);
+  return a1 + (b + b3 + sqrt_fast(d3)) * (1.0f / 3.0f);
 }
 
-__device__ __forceinline__ double local_solve(double ax, double ay, double az, double s) {
-  const double lo = fmin(ax, ay), hi = fmax(ax, ay);
-  const double a1 = fmin(lo, az), mid = fmax(lo, az);
-  const double a2 = fmin(hi, mid), a3 = fmax(hi, mid);
+// Values are stored relative to the smallest exit value, so every value is
+// >= 0 or +inf and two doubles order like their bit patterns: the FP64
+// min / max / compare run on the integer pipes, leaving the (narrow) FP64
+// pipe to the arithmetic.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ double dmin_nn(double a, double b) {
+  const long long ia = dbits(a), ib = dbits(b);
+  return __longlong_as_double(ia < ib ? ia : ib);
+}
+__device__ __forceinline__ double dmax_nn(double a, double b) {
+  const long long ia = dbits(a), ib = dbits(b);
+  return __longlong_as_double(ia < ib ? ib : ia);
+}
+__device__ __forceinline__ bool dle_nn(double a, double b) { return dbits(a) <= dbits(b); }
+
+// Direct FP64 evaluation of the same root (used by the residual check).
+__device__ __forceinline__ double local_solve_direct(double ax, double ay, double az, double s) {
+  const double lo = dmin_nn(ax, ay), hi = dmax_nn(ax, ay);
+  const double a1 = dmin_nn(lo, az), mid = dmax_nn(lo, az);
+  const double a2 = dmin_nn(hi, mid), a3 = dmax_nn(hi, mid);
   const double u1 = a1 + s;
-  if (u1 <= a2) return u1;
+  if (dle_nn(u1, a2)) return u1;  // also covers a1 = +inf (returns +inf)
   const double s2 = s * s;
   const double b = a2 - a1;
   const double u2 = a1 + 0.5 * (b + sqrt(fmax(2.0 * s2 - b * b, 0.0)));
-  if (u2 <= a3) return u2;
+  if (dle_nn(u2, a3)) return u2;
   const double b3 = a3 - a1, e = b3 - b;
   const double d3 = 3.0 * s2 - (b * b + b3 * b3 + e * e);
-  return a1 + (b + b3 + sqrt(fmax(d3, 0.0))) / 3.0;
+  return a1 + (b + b3 + sqrt(fmax(d3, 0.0))) * 0.33333333333333331;
 }
+
+// FP64 local solve used by the sweeps: the shifted root w = U - a1 of
+//   f(w) = sum_{d<=m} (w - b_d)^2 - s^2 = 0,   b_d = a_d - a1,
+// is first found in FP32 (term count m, and w32 to ~1e-7 relative), then
+// refined by one Newton step in FP64:  w = w32 - f(w32) / f'(w32), with
+// f'(w) = 2 sum_{d<=m} (w - b_d) >= 2w >= 2s/sqrt(3).  Newton's error after
+// one step is ~ m e0^2 / f', i.e. ~1e-14 s, below an FP64 ulp of U; f' only
+// scales the tiny correction, so it is taken in FP32.  The one-term root is
+// exact (U = a1 + s).  Near a branch boundary the m-term roots of both
+// branches agree to O(e0^2 / s), so the FP32 choice of m costs nothing.
+__device__ __forceinline__ double local_solve(double ax, double ay, double az, double s) {
+  const double lo = dmin_nn(ax, ay), hi = dmax_nn(ax, ay);
+  const double a1 = dmin_nn(lo, az), mid = dmax_nn(lo, az);
+  const double a2 = dmin_nn(hi, mid), a3 = dmax_nn(hi, mid);
+  const double u1 = a1 + s;
+  if (dle_nn(u1, a2)) return u1;  // one term, exact; also a1 = +inf
+  const double b2 = a2 - a1, b3 = a3 - a1;
+  const float fs = (float)s, fb2 = (float)b2, fb3 = (float)b3;
+  const float fs2 = fs * fs;
+  const float w2 = 0.5f * (fb2 + sqrtf(fmaxf(2.0f * fs2 - fb2 * fb2, 0.0f)));
+  const double s2 = s * s;
+  if (w2 <= fb3) {
+    const double w = (double)w2, r2 = w - b2;
+    const double f = fma(w, w, fma(r2, r2, -s2));
+    const float rinv = 0.5f / (2.0f * w2 - fb2);
+    return a1 + (w - f * (double)rinv);
+  }
+  const float e = fb3 - fb2;
+  const float d3 = 3.0f * fs2 - (fb2 * fb2 + fb3 * fb3 + e * e);
+  const float w3 = (fb2 + fb3 + sqrtf(fmaxf(d3, 0.0f))) * (1.0f / 3.0f);
+  const double w = (double)w3, r2 = w - b2, r3 = w - b3;
+  const double f = fma(w, w, fma(r2, r2, fma(r3, r3, -s2)));
+  const float rinv = 0.5f / (3.0f * w3 - fb2 - fb3);
+  return a1 + (w - f * (double)rinv);
+}
+
+// Axis minimum of two neighbour values.
+__device__ __forceinline__ float nmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double nmin(double a, double b) { return dmin_nn(a, b); }
 
 template <typename T>
 __device__ __forceinline__ T tinf();
@@ -208,12 +271,15 @@ __device__ __forceinline__ double tinf<double>() { return CUDART_INF; }
 // Bucket b (an absolute, ever-growing index) holds cells whose key lies in
 // [base + b/inv_width, base + (b+1)/inv_width); it lives in ring slot
 // b mod kNumBuckets as a lock-free stack (Treiber stack with a 32-bit ABA
-// tag in the head word).  `cur` is a lower bound of the lowest non-empty
-// bucket: a push lowers it with atomicMin, a worker that finds bucket `cur`
-// empty moves it to the next non-empty bucket and re-checks the buckets it
-// skipped, so a push that raced the move is not stranded.  Within a bucket
-// the order is arbitrary, as is the order among cells of equal priority in
-// the paper; the final values do not depend on it (Sec. 4, cell values).
+// tag in the head word).  `cur` is the bucket being processed.  Workers
+// take cells only from bucket `cur`, and `cur` moves on only when its stack
+// is empty AND no cell taken from it is still being swept (run[slot] == 0):
+// the buckets are processed in order, like the heap of Alg. 1 processes
+// cells in order of their values, while all cells of one bucket run in
+// parallel.  A push into a lower bucket lowers `cur` (atomicMin).  A worker
+// that moves `cur` forward re-checks the buckets it skipped, so a push that
+// raced the move is not stranded.  Within a bucket the order is arbitrary;
+// the final values do not depend on the processing order (Sec. 4).
 
 __device__ __forceinline__ void stack_push(const CellArrays& c, unsigned slot, unsigned cell) {
   unsigned long long* head = c.heads + slot;
@@ -247,6 +313,10 @@ __device__ __forceinline__ int stack_pop(const CellArrays& c, unsigned slot) {
   }
 }
 
+__device__ __forceinline__ bool stack_empty(const CellArrays& c, unsigned slot) {
+  return (unsigned)(ld_acquire_u64(c.heads + slot) & 0xffffffffull) == 0u;
+}
+
 __device__ __forceinline__ unsigned bucket_of(const Control* ctl, float keyf, unsigned cur) {
   if (!(keyf < CUDART_INF_F)) return cur;  // no usable key: take it soon
   float f = (keyf - ctl->base) * ctl->inv_width;
@@ -265,90 +335,124 @@ __device__ __forceinline__ void queue_push(const CellArrays& c, Control* ctl, un
   const unsigned b = bucket_of(ctl, keyf, cur);
   atomicAdd(&ctl->queued, 1);
   stack_push(c, b & kBucketMask, cell);
+  __threadfence();
   atomicMin(&ctl->cur, b);
   ++*pushes;
 }
 
+// First non-empty bucket at offset 1..kNumBuckets-1 after `cur`, or
+// kNumBuckets (warp-collective).  Looks 128 buckets ahead, then, if cells
+// are queued further on, around the whole ring.
+__device__ __forceinline__ int scan_next_bucket(const CellArrays& c, unsigned cur, bool full,
+                                                int lane) {
+  const int limit = full ? kNumBuckets : 129;
+  for (int base = 1; base < limit; base += 128) {
+    unsigned m = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int o = base + r * 32 + lane;
+      const bool ne = o < kNumBuckets &&
+                      (unsigned)(ld_relaxed_u64(c.heads + ((cur + (unsigned)o) & kBucketMask)) &
+                                 0xffffffffull) != 0u;
+      const unsigned bal = __ballot_sync(0xffffffffu, ne);
+      if (bal && m == 0) m = (unsigned)(base + r * 32 + __ffs(bal) - 1);
+    }
+    if (m) return (int)m;
+  }
+  return kNumBuckets;
+}
+
 // Warp-collective pop (all 32 lanes of the calling warp).  Returns a cell
-// whose state is now RUNNING, or -1 when the solve is finished or failed.
-static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl, unsigned long long spin_cap_ns,
-                              int lane) {
+// whose state is now RUNNING (and the ring slot it came from in *slot_out),
+// or -1 when the solve is finished or failed.
+static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
+                                     unsigned long long spin_cap_ns, int lane,
+                                     unsigned* slot_out, bool relaxed) {
   unsigned last_prog = 0xffffffffu;
   unsigned long long t_idle = 0;
-  unsigned backoff = 32;
+  unsigned backoff = 64;
+  unsigned polls = 0;
   for (;;) {
-    int stop = 0, cell = -1;
+    int stop = 0, cell = -1, can_advance = 0;
     unsigned cur = 0;
     if (lane == 0) {
-      stop = (ld_acquire_s32(&ctl->status) != 0) || (ld_acquire_s32(&ctl->active) <= 0);
+      // The fast path of a poll reads two words (cur and its stack head);
+      // termination, errors and bucket completion are checked every 4th
+      // empty poll, to keep the traffic of waiting workers on the shared
+      // control words low.
+      const bool full_check = (polls & 3u) == 0u;
+      if (full_check)
+        stop = (ld_acquire_s32(&ctl->status) != 0) || (ld_acquire_s32(&ctl->active) <= 0);
       if (!stop) {
         cur = ld_acquire_u32(&ctl->cur);
-        cell = stack_pop(c, cur & kBucketMask);
-        if (cell >= 0) {
-          atomicSub(&ctl->queued, 1);
-          // QUEUED -> RUNNING (drops DIRTY: this visit loads the newest data)
-          unsigned st = ld_relaxed_u32(c.state + cell);
-          for (;;) {
-            if (!(st & kStQueued)) {
-              set_status(ctl, EIK_EQUEUE);
-              cell = -1;
-              stop = 1;
-              break;
+        const unsigned slot = cur & kBucketMask;
+        if (!stack_empty(c, slot)) {
+          atomicAdd(c.run + slot, 1);  // reserve before taking: blocks an advance
+          cell = stack_pop(c, slot);
+          if (cell < 0) {
+            atomicSub(c.run + slot, 1);
+          } else {
+            atomicSub(&ctl->queued, 1);
+            // QUEUED -> RUNNING (drops DIRTY: this visit loads the newest data)
+            unsigned st = ld_relaxed_u32(c.state + cell);
+            for (;;) {
+              if (!(st & kStQueued)) {
+                set_status(ctl, EIK_EQUEUE);
+                cell = -1;
+                stop = 1;
+                break;
+              }
+              const unsigned prev = atomicCAS(c.state + cell, st, kStRunning);
+              if (prev == st) break;
+              st = prev;
             }
-            const unsigned prev = atomicCAS(c.state + cell, st, kStRunning);
-            if (prev == st) break;
-            st = prev;
+            __threadfence();
+            *slot_out = slot;
           }
-          __threadfence();
+        } else if (full_check) {
+          // strict order: the bucket is done when no cell taken from it is
+          // still running; relaxed order: as soon as its stack is empty
+          can_advance = (relaxed || ld_acquire_s32(c.run + slot) == 0) && stack_empty(c, slot);
         }
       }
+      ++polls;
     }
     stop = __shfl_sync(0xffffffffu, stop, 0);
     if (stop) return -1;
     cell = __shfl_sync(0xffffffffu, cell, 0);
     if (cell >= 0) return cell;
     cur = __shfl_sync(0xffffffffu, cur, 0);
+    can_advance = __shfl_sync(0xffffffffu, can_advance, 0);
 
-    // Bucket `cur` is empty.  Look further only if some cell is queued.
-    int queued = 0;
-    if (lane == 0) queued = ld_acquire_s32(&ctl->queued);
-    queued = __shfl_sync(0xffffffffu, queued, 0);
-    if (queued > 0) {
-      int found = kNumBuckets;
-      for (int base = 1; base < kNumBuckets && found == kNumBuckets; base += 128) {
-        unsigned m = 0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int o = base + r * 32 + lane;
-          const bool ne = o < kNumBuckets &&
-                          (unsigned)(ld_relaxed_u64(c.heads + ((cur + (unsigned)o) & kBucketMask)) &
-                                     0xffffffffull) != 0u;
-          const unsigned bal = __ballot_sync(0xffffffffu, ne);
-          if (bal && m == 0) m = (unsigned)(base + r * 32 + __ffs(bal) - 1);
-        }
-        if (m) found = (int)m;
-      }
-      if (found < kNumBuckets) {
-        if (lane == 0) {
-          if (atomicCAS(&ctl->cur, cur, cur + (unsigned)found) == cur) {
-            __threadfence();
-            for (int o = 0; o < found; ++o) {
-              const unsigned sl = (cur + (unsigned)o) & kBucketMask;
-              if ((unsigned)(ld_acquire_u64(c.heads + sl) & 0xffffffffull) != 0u) {
-                atomicMin(&ctl->cur, cur + (unsigned)o);
-                break;
+    if (can_advance) {
+      // bucket `cur` is finished: move to the next non-empty bucket
+      int queued = 0;
+      if (lane == 0) queued = ld_acquire_s32(&ctl->queued);
+      queued = __shfl_sync(0xffffffffu, queued, 0);
+      if (queued > 0) {
+        int found = scan_next_bucket(c, cur, false, lane);
+        if (found == kNumBuckets) found = scan_next_bucket(c, cur, true, lane);
+        if (found < kNumBuckets) {
+          if (lane == 0) {
+            if (atomicCAS(&ctl->cur, cur, cur + (unsigned)found) == cur) {
+              __threadfence();
+              for (int o = 0; o < found; ++o) {
+                if (!stack_empty(c, (cur + (unsigned)o) & kBucketMask)) {
+                  atomicMin(&ctl->cur, cur + (unsigned)o);
+                  break;
+                }
               }
             }
           }
+          __syncwarp();
+          backoff = 64;
+          continue;
         }
-        __syncwarp();
-        backoff = 32;
-        continue;
       }
     }
     // Nothing to take: wait for running cells, with a no-progress limit.
     int timed_out = 0;
-    if (lane == 0) {
+    if (lane == 0 && (polls & 15u) == 1u) {
       const unsigned prog = ld_acquire_u32(&ctl->progress);
       const unsigned long long now = global_timer_ns();
       if (prog != last_prog) {
@@ -362,7 +466,7 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl, unsigned
     timed_out = __shfl_sync(0xffffffffu, timed_out, 0);
     if (timed_out) return -1;
     __nanosleep(backoff);
-    if (backoff < 1024) backoff *= 2;
+    if (backoff < 16384) backoff *= 2;
   }
 }
 
@@ -373,9 +477,13 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl, unsigned
 // caller has made its new border values visible (__threadfence) before.
 __device__ __forceinline__ void flag_cell(const CellArrays& c, Control* ctl, unsigned nb,
                                           unsigned key, unsigned dirbits,
-                                          unsigned long long* pushes) {
+                                          unsigned long long* pushes, bool gated = false) {
   atomicMin(c.key + nb, key);
   atomicOr(c.dir + nb, dirbits);
+  // Polish schedule: a cell whose upwind neighbours have not all finished a
+  // first visit is not queued yet; that first visit comes later and loads
+  // this data (the read-modify-write orders it before the release).
+  if (gated && atomicAdd(c.deps + nb, 0) > 0) return;
   const unsigned old = atomicOr(c.state + nb, kStDirty);
   if ((old & (kStQueued | kStRunning | kStDirty)) == 0u) {
     atomicAdd(&ctl->active, 1);
@@ -385,11 +493,12 @@ __device__ __forceinline__ void flag_cell(const CellArrays& c, Control* ctl, uns
   }
 }
 
-// End of a visit: RUNNING -> IDLE, or RUNNING|DIRTY -> QUEUED with a re-push.
-// The active count drops only after every flag of this visit (Sec. 5: the
+// End of a visit: RUNNING -> IDLE, or RUNNING|DIRTY -> QUEUED with a re-push;
+// then the bucket the cell came from counts one running cell less.  The
+// active count drops only after every flag of this visit (Sec. 5: the
 // counter is decremented after processing so no worker quits early).
 __device__ __forceinline__ void retire_cell(const CellArrays& c, Control* ctl, unsigned cell,
-                                            unsigned long long* pushes) {
+                                            unsigned slot, unsigned long long* pushes) {
   unsigned st = ld_relaxed_u32(c.state + cell);
   unsigned nw;
   for (;;) {
@@ -398,14 +507,13 @@ __device__ __forceinline__ void retire_cell(const CellArrays& c, Control* ctl, u
     if (prev == st) break;
     st = prev;
   }
+  __threadfence();
   if (nw == kStQueued) {
-    __threadfence();
     queue_push(c, ctl, cell, pushes);
-  } else {
     __threadfence();
-    atomicSub(&ctl->active, 1);
   }
-  atomicAdd(&ctl->progress, 1u);
+  atomicSub(c.run + slot, 1);
+  if (nw != kStQueued) atomicSub(&ctl->active, 1);
 }
 
 }  // namespace eik

@@ -35,6 +35,11 @@ enum CounterIndex {
   kCntUpdates,
   kCntPushes,
   kCntMaxSweeps,  // largest sweep count of one visit (atomicMax)
+  kCntBusyNs,     // sum over visits of pop-to-retire time (ns)
+  kCntStageNs,    // ... of which: TMA staging
+  kCntSweepNs,    //               sweeps
+  kCntFlagNs,     //               write-back and flags
+  kCntPopNs,      // time spent in the pop loop (waiting included)
   kNumCounters
 };
 
@@ -50,25 +55,31 @@ struct Instance {
   double kappa;          // change threshold of Sec. 6.4
 };
 
-// Queue and solver control words, one block in device memory.
+// Queue and solver control words, one block in device memory.  The words
+// that every waiting worker polls sit on cache lines of their own so that
+// the polling does not queue behind the atomics of working workers.
 struct Control {
-  unsigned cur;        // absolute index of the lowest possibly non-empty bucket
-  int active;          // cells QUEUED or RUNNING
-  int queued;          // cells sitting in a bucket stack
-  int status;          // first error code (EIK_*), 0 = fine
-  unsigned progress;   // retired cell visits
-  int n_sources;       // exit nodes seen by the init kernel
-  float base;          // key of bucket 0
-  float inv_width;     // 1 / bucket width
-  double sum_s;        // sum of s over non-exit nodes (bucket width estimate)
-  unsigned long long n_s;          // number of terms in sum_s
+  alignas(128) unsigned cur;  // absolute index of the bucket being processed
+  alignas(128) int active;    // cells QUEUED or RUNNING
+  alignas(128) int queued;    // cells sitting in a bucket stack
+  alignas(128) int status;    // first error code (EIK_*), 0 = fine
+  alignas(128) unsigned progress;  // retired cell visits
+  alignas(128) float base;    // key of bucket 0
+  double kappa_bulk;          // change threshold of the FP32 bulk pass
+  float inv_width;            // 1 / bucket width
+  int n_sources;              // exit nodes seen by the init kernel
+  int bad_input;              // an input failed validation
+  double sum_s;               // sum of s over non-exit nodes (bucket width estimate)
+  unsigned long long n_s;     // number of terms in sum_s
   unsigned long long min_q_ord;    // ordered bits of min q (double)
   unsigned long long umax_bits;    // ordered bits of the largest finite u
-  unsigned long long resid_bits;   // bits of the largest residual (>= 0)
+                                   // (of the lifted start, during the polish)
+  unsigned long long final_umax_bits;  // ... of the final u
+  unsigned long long resid_bits;   // bits of the largest final residual (>= 0)
+  unsigned long long check_bits;   // bits of the largest (Lambda(u) - u) after
+                                   // the monotone polish (> 0: u below the fixed point)
   unsigned long long nonfinite;
-  unsigned long long counters[2][kNumCounters];  // [bulk, polish]
-  int bad_input;       // an input failed validation
-  int pad[3];
+  unsigned long long counters[3][kNumCounters];  // [bulk, polish, polish fallback]
 };
 
 struct CellArrays {
@@ -78,6 +89,10 @@ struct CellArrays {
   int* inst;                     // instance of each cell
   unsigned* next;                // stack links: next cell + 1, 0 = end
   unsigned long long* heads;     // [kNumBuckets] (tag << 32) | (top cell + 1)
+  int* run;                      // [kNumBuckets] cells taken from a bucket, not retired
+  // Polish schedule (dependency graph read off the FP32 result):
+  int* deps;                     // upwind neighbours still to finish a first visit
+  unsigned* down;                // bits 0-5: downwind faces; bit 8: first visit done
 };
 
 struct CellKernelParams {
@@ -89,7 +104,11 @@ struct CellKernelParams {
   const int* plane_off;             // plane start offsets, 3(n-1)+2 entries
   unsigned long long spin_cap_ns;
   int max_sweeps;
-  int pass;                         // 0 = bulk counters, 1 = polish counters
+  int pass;                         // counter set: 0 bulk, 1 polish, 2 fallback
+  int max_ctas;                     // grid limit (0 = every co-resident CTA)
+  int kappa_from_ctl;               // 1: take kappa from ctl->kappa_bulk
+  int relaxed;                      // 1: move past a bucket once its stack is empty
+  int gated;                        // 1: polish schedule (cells wait for deps == 0)
 };
 
 }  // namespace eik

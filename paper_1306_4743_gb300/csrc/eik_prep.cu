@@ -22,6 +22,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Cell values of the cells that hold an exit node (Sec. 4: V^c = min q over
+// the cell's exit nodes).  The LSM initialisation also marks the grid
+// neighbours of exit nodes active; a neighbour across a cell face lies in
+// another cell, which must be queued as well (an exit value never changes,
+// so no face flag would reach that cell otherwise).
+__device__ __forceinline__ void mark_exit_cells(const CellArrays& c, int cell_base, int ncx, int ncy,
+                                                int ncz, int N, int lc, int a, int b, int cc,
+                                                int cx, int cy, int cz, unsigned kq) {
+  atomicMin(c.key + cell_base + lc, kq);
+  if (a == 0 && cx > 0) atomicMin(c.key + cell_base + lc - 1, kq);
+  if (a == N - 1 && cx + 1 < ncx) atomicMin(c.key + cell_base + lc + 1, kq);
+  if (b == 0 && cy > 0) atomicMin(c.key + cell_base + lc - ncx, kq);
+  if (b == N - 1 && cy + 1 < ncy) atomicMin(c.key + cell_base + lc + ncx, kq);
+  if (cc == 0 && cz > 0) atomicMin(c.key + cell_base + lc - ncx * ncy, kq);
+  if (cc == N - 1 && cz + 1 < ncz) atomicMin(c.key + cell_base + lc + ncx * ncy, kq);
+}
+
 template <typename T>
 __global__ void reset_cells_kernel(const PrepInstance* __restrict__ pi, int count, CellArrays c) {
   const int ii = blockIdx.y;
@@ -38,12 +55,52 @@ __global__ void reset_cells_kernel(const PrepInstance* __restrict__ pi, int coun
   }
 }
 
-// Padded u: +inf everywhere except exit nodes, which hold q.
-template <typename T>
-__global__ void init_u_kernel(const PrepInstance* __restrict__ pi, int count) {
+// Smallest exit value over the launch, exit-node counts, q validation.  The
+// solver works on u - q_min internally (the system is shift invariant), so
+// every stored value is >= 0 and orders like its bit pattern.
+__global__ void minq_kernel(const PrepInstance* __restrict__ pi, int count, Control* ctl,
+                            int* n_src) {
   const int ii = blockIdx.y;
   if (ii >= count) return;
   const PrepInstance P = pi[ii];
+  const long long total = (long long)P.nx * P.ny * P.nz;
+  unsigned long long minq = ~0ull;
+  int nsrc = 0, bad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (P.mask[e]) {
+      const double qv = P.q[e];
+      if (!isfinite(qv)) bad = 1;
+      ++nsrc;
+      const unsigned long long o = ord_of_double(qv);
+      minq = o < minq ? o : minq;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    nsrc += __shfl_xor_sync(0xffffffffu, nsrc, o);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, minq, o);
+    minq = w < minq ? w : minq;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nsrc) atomicAdd(n_src + ii, nsrc);
+    if (bad) atomicExch(&ctl->bad_input, 1);
+    if (minq != ~0ull) atomicMin(&ctl->min_q_ord, minq);
+  }
+}
+
+__device__ __forceinline__ double q_base(const Control* ctl) {
+  const double b = double_of_ord(ctl->min_q_ord);
+  return isfinite(b) ? b : 0.0;
+}
+
+// Padded u: +inf everywhere except exit nodes, which hold q - q_min.
+template <typename T>
+__global__ void init_u_kernel(const PrepInstance* __restrict__ pi, int count, const Control* ctl) {
+  const int ii = blockIdx.y;
+  if (ii >= count) return;
+  const PrepInstance P = pi[ii];
+  const double qb = q_base(ctl);
   T* u = static_cast<T*>(P.u);
   const long long total = P.px * P.py * P.pz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -52,7 +109,7 @@ __global__ void init_u_kernel(const PrepInstance* __restrict__ pi, int count) {
     T v = tinf<T>();
     if (x >= 1 && x <= P.nx && y >= 1 && y <= P.ny && z >= 1 && z <= P.nz) {
       const long long lin = (x - 1) + P.nx * ((y - 1) + (long long)P.ny * (z - 1));
-      if (P.mask[lin]) v = (T)P.q[lin];
+      if (P.mask[lin]) v = (T)(P.q[lin] - qb);
     }
     u[e] = v;
   }
@@ -64,7 +121,7 @@ __global__ void init_u_kernel(const PrepInstance* __restrict__ pi, int count) {
 // hold a grid neighbour of an exit node; input validation.
 template <typename T>
 __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, int count, CellArrays c,
-                              Control* ctl, int* n_src) {
+                              Control* ctl) {
   const int ii = blockIdx.y;
   if (ii >= count) return;
   const PrepInstance P = pi[ii];
@@ -72,10 +129,10 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, int count, Ce
   T* s = static_cast<T*>(P.s);
   double* s64 = static_cast<double*>(P.s64);
   const long long total = (long long)P.ncells * N3;
+  const double qb = q_base(ctl);
   double acc = 0.0;
   unsigned long long cnt = 0;
-  int bad = 0, nsrc = 0;
-  unsigned long long minq = ~0ull;
+  int bad = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int lc = (int)(e / N3), r = (int)(e % N3);
@@ -86,24 +143,8 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, int count, Ce
     if (i < P.nx && j < P.ny && k < P.nz) {
       const long long lin = i + P.nx * (j + (long long)P.ny * k);
       if (P.mask[lin]) {
-        const double qv = P.q[lin];
-        if (!isfinite(qv)) bad = 1;
-        ++nsrc;
-        const unsigned kq = key_of((T)qv);
-        atomicMin(c.key + P.cell_base + lc, kq);
-        // The LSM initialisation marks the grid neighbours of exit nodes
-        // active; a neighbour across a cell face lies in another cell, which
-        // must be queued as well (an exit value never changes, so no face
-        // flag would reach that cell otherwise).
-        if (a == 0 && cx > 0) atomicMin(c.key + P.cell_base + lc - 1, kq);
-        if (a == N - 1 && cx + 1 < P.ncx) atomicMin(c.key + P.cell_base + lc + 1, kq);
-        if (b == 0 && cy > 0) atomicMin(c.key + P.cell_base + lc - P.ncx, kq);
-        if (b == N - 1 && cy + 1 < P.ncy) atomicMin(c.key + P.cell_base + lc + P.ncx, kq);
-        if (cc == 0 && cz > 0) atomicMin(c.key + P.cell_base + lc - P.ncx * P.ncy, kq);
-        if (cc == N - 1 && cz + 1 < P.ncz)
-          atomicMin(c.key + P.cell_base + lc + P.ncx * P.ncy, kq);
-        const unsigned long long o = ord_of_double(qv);
-        minq = o < minq ? o : minq;
+        mark_exit_cells(c, P.cell_base, P.ncx, P.ncy, P.ncz, N, lc, a, b, cc, cx, cy, cz,
+                        key_of((T)(P.q[lin] - qb)));
       } else {
         const float f = P.F[lin];
         if (!(f > 0.0f) || isinf(f)) {
@@ -121,25 +162,20 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, int count, Ce
   acc = warp_sum(acc);
   for (int o = 16; o; o >>= 1) {
     cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    nsrc += __shfl_xor_sync(0xffffffffu, nsrc, o);
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    const unsigned long long w = __shfl_xor_sync(0xffffffffu, minq, o);
-    minq = w < minq ? w : minq;
   }
   if ((threadIdx.x & 31) == 0) {
     if (cnt) {
       atomicAdd(&ctl->sum_s, acc);
       atomicAdd(&ctl->n_s, cnt);
     }
-    if (nsrc) atomicAdd(n_src + ii, nsrc);
     if (bad) atomicExch(&ctl->bad_input, 1);
-    if (minq != ~0ull) atomicMin(&ctl->min_q_ord, minq);
   }
 }
 
 // Validation verdict, queue origin and bucket width.
 __global__ void setup_bulk_kernel(Control* ctl, const int* n_src, int count, int n,
-                                  double width_factor) {
+                                  double width_factor, double kappa_rel) {
   if (threadIdx.x || blockIdx.x) return;
   int ok = !ctl->bad_input;
   for (int t = 0; t < count; ++t)
@@ -148,19 +184,23 @@ __global__ void setup_bulk_kernel(Control* ctl, const int* n_src, int count, int
     set_status(ctl, EIK_EINVAL);
     return;
   }
-  const double qmin = double_of_ord(ctl->min_q_ord);
   const double mean_s = ctl->n_s ? ctl->sum_s / (double)ctl->n_s : 1.0;
   double width = width_factor * (double)n * mean_s;
   if (!(width > 0.0) || !isfinite(width)) width = 1.0;
-  ctl->base = __double2float_rd(qmin);
+  ctl->base = 0.0f;  // values are stored relative to q_min
   ctl->inv_width = (float)(1.0 / width);
+  // change threshold of the FP32 bulk pass in polish mode: stop passing on
+  // changes of a few FP32 ulps of a value one cell away from the exit set
+  // (stopping early only leaves values high; the polish starts above the
+  // fixed point either way)
+  ctl->kappa_bulk = kappa_rel * (double)n * mean_s;
   ctl->cur = 0u;
   ctl->active = 0;
   ctl->queued = 0;
 }
 
 // Queue every cell that holds an exit node (Alg. 1 l.2).
-__global__ void seed_sources_kernel(int total_cells, CellArrays c, Control* ctl) {
+__global__ void seed_sources_kernel(int total_cells, CellArrays c, Control* ctl, int pass) {
   if (ctl->status) return;
   unsigned long long pushes = 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_cells;
@@ -172,7 +212,7 @@ __global__ void seed_sources_kernel(int total_cells, CellArrays c, Control* ctl)
       queue_push(c, ctl, (unsigned)g, &pushes);
     }
   }
-  if (pushes) atomicAdd(&ctl->counters[0][kCntPushes], pushes);
+  if (pushes) atomicAdd(&ctl->counters[pass][kCntPushes], pushes);
 }
 
 // FP32 result -> FP64 padded array of the polish; largest finite value.
@@ -180,6 +220,7 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, int coun
   const int ii = blockIdx.y;
   if (ii >= count) return;
   const PolishInstance P = pi[ii];
+  const double qb = q_base(ctl);
   const float* u32 = static_cast<const float*>(P.u32);
   double* u64 = static_cast<double*>(P.u64);
   const long long total = P.px64 * P.py * P.pz;
@@ -190,7 +231,17 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, int coun
     double v = CUDART_INF;
     if (x >= 1 && x <= P.nx && y >= 1 && y <= P.ny && z >= 1 && z <= P.nz) {
       const long long lin = (x - 1) + P.nx * ((y - 1) + (long long)P.ny * (z - 1));
-      v = P.mask[lin] ? P.q[lin] : (double)u32[x + P.px32 * (y + P.py * z)];
+      if (P.mask[lin]) {
+        v = P.q[lin] - qb;
+      } else {
+        // Lift the FP32 value above the FP64 fixed point: its rounding error
+        // grows at most ~2^-24 u per node along a characteristic (u is
+        // stored relative to q_min), so a lift of 2^-11 u covers paths of up
+        // to 2^13 nodes.  The monotone FP64 sweeps then descend to the fixed
+        // point.
+        v = (double)u32[x + P.px32 * (y + P.py * z)];
+        v += v * 4.8828125e-4;
+      }
       if (isfinite(v)) {
         const unsigned long long o = ord_of_double(v);
         mx = o > mx ? o : mx;
@@ -203,10 +254,19 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, int coun
 
 // Polish cell values: the smallest value of the cell's non-fixed nodes, so
 // that the polish visits cells in the causal order of the FP32 result.
+// A gated launch runs only when the monotone polish left some u below the
+// fixed point (check > threshold): the replace-mode fallback.
+__device__ __forceinline__ bool fallback_needed(const Control* ctl, double kappa) {
+  const double check = __longlong_as_double((long long)ctl->check_bits);
+  const double umax = double_of_ord(ctl->umax_bits);
+  return check > kappa + 1e-13 * fmax(fabs(umax), 1.0);
+}
+
 __global__ void polish_keys_kernel(const PolishInstance* __restrict__ pi, int count,
-                                   CellArrays c) {
+                                   CellArrays c, const Control* ctl, int gated, double kappa) {
   const int ii = blockIdx.y;
   if (ii >= count) return;
+  if (gated && (ctl->status || !fallback_needed(ctl, kappa))) return;
   const PolishInstance P = pi[ii];
   const int N = P.n, N3 = N * N * N;
   const double* u64 = static_cast<const double*>(P.u64);
@@ -216,28 +276,132 @@ __global__ void polish_keys_kernel(const PolishInstance* __restrict__ pi, int co
   for (int lc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; lc < P.ncells; lc += warps) {
     const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
     double m = CUDART_INF;
+    int at = 0;
     for (int r = lane; r < N3; r += 32) {
       if (!(s64[(long long)lc * N3 + r] < CUDART_INF)) continue;
       const int a = r % N, b = (r / N) % N, cc = r / (N * N);
       const long long x = (long long)N * cx + a + 1, y = (long long)N * cy + b + 1,
                       z = (long long)N * cz + cc + 1;
       const double v = u64[x + P.px64 * (y + P.py * z)];
-      m = v < m ? v : m;
+      if (v < m) {
+        m = v;
+        at = r;
+      }
     }
-    for (int o = 16; o; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o; o >>= 1) {
+      const double mo = __shfl_xor_sync(0xffffffffu, m, o);
+      const int ao = __shfl_xor_sync(0xffffffffu, at, o);
+      if (mo < m || (mo == m && ao < at)) {
+        m = mo;
+        at = ao;
+      }
+    }
     if (lane == 0) {
       const int g = P.cell_base + lc;
       c.key[g] = key_of(m);
       c.state[g] = 0u;
-      c.dir[g] = 0u;
+      // first sweep: away from the cell's smallest FP32 value (its upwind side)
+      const int a = at % N, b = (at / N) % N, cc = at / (N * N);
+      const int d = (a >= N / 2 ? 1 : 0) | (b >= N / 2 ? 2 : 0) | (cc >= N / 2 ? 4 : 0);
+      c.dir[g] = 1u << d;
       c.next[g] = 0u;
     }
   }
 }
 
-__global__ void setup_polish_kernel(Control* ctl) {
+// Dependency graph of the polish, read off the FP32 result.  Across each
+// face, B feeds C when some border node of C (not fixed) has a larger value
+// than its neighbour in B.  An edge B -> C is kept only when B's cell value
+// is below C's (ties: lower cell id), so the kept graph is acyclic; deps[C]
+// counts kept incoming edges, down[C] marks kept outgoing faces.  A cell is
+// queued once deps[C] reaches 0; an edge that was dropped is still honoured
+// by the flag protocol, which re-queues C if B's later values reach it.
+__global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi, int count,
+                                    CellArrays c) {
+  const int ii = blockIdx.y;
+  if (ii >= count) return;
+  const PolishInstance P = pi[ii];
+  const int N = P.n, N3 = N * N * N;
+  const double* u64 = static_cast<const double*>(P.u64);
+  const double* s64 = static_cast<const double*>(P.s64);
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const long long sy = P.px64, sz = P.px64 * P.py;
+  for (int lc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; lc < P.ncells; lc += warps) {
+    const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
+    const int g = P.cell_base + lc;
+    const unsigned kc = c.key[g];
+    int deps = 0;
+    unsigned down = 0;
+    for (int f = 0; f < 6; ++f) {
+      const int axis = f >> 1, upper = f & 1;
+      const int ncoord = (axis == 0 ? cx : axis == 1 ? cy : cz) + (upper ? 1 : -1);
+      const int nlim = axis == 0 ? P.ncx : axis == 1 ? P.ncy : P.ncz;
+      if (ncoord < 0 || ncoord >= nlim) continue;
+      const int nlc = axis == 0 ? lc + (upper ? 1 : -1)
+                    : axis == 1 ? lc + (upper ? P.ncx : -P.ncx)
+                                : lc + (upper ? P.ncx * P.ncy : -P.ncx * P.ncy);
+      bool in = false, out = false;
+      for (int q = lane; q < N * N; q += 32) {
+        const int a = q % N, b = q / N;
+        int i, j, k;
+        if (axis == 0) { i = upper ? N - 1 : 0; j = a; k = b; }
+        else if (axis == 1) { i = a; j = upper ? N - 1 : 0; k = b; }
+        else { i = a; j = b; k = upper ? N - 1 : 0; }
+        const long long gi = (long long)N * cx + i, gj = (long long)N * cy + j,
+                        gk = (long long)N * cz + k;
+        if (gi >= P.nx || gj >= P.ny || gk >= P.nz) continue;
+        // neighbour node across the face, in cell nlc
+        int i2 = i, j2 = j, k2 = k;
+        if (axis == 0) i2 = upper ? 0 : N - 1;
+        else if (axis == 1) j2 = upper ? 0 : N - 1;
+        else k2 = upper ? 0 : N - 1;
+        const long long gi2 = gi + (axis == 0 ? (upper ? 1 : -1) : 0);
+        const long long gj2 = gj + (axis == 1 ? (upper ? 1 : -1) : 0);
+        const long long gk2 = gk + (axis == 2 ? (upper ? 1 : -1) : 0);
+        if (gi2 >= P.nx || gj2 >= P.ny || gk2 >= P.nz) continue;
+        const double uc = u64[(gi + 1) + sy * (gj + 1) + sz * (gk + 1)];
+        const double ub = u64[(gi2 + 1) + sy * (gj2 + 1) + sz * (gk2 + 1)];
+        const bool c_free = s64[(long long)lc * N3 + i + N * (j + N * k)] < CUDART_INF;
+        const bool b_free = s64[(long long)nlc * N3 + i2 + N * (j2 + N * k2)] < CUDART_INF;
+        if (c_free && ub < uc) in = true;
+        if (b_free && uc < ub) out = true;
+      }
+      in = __any_sync(0xffffffffu, in);
+      out = __any_sync(0xffffffffu, out);
+      const int gb = P.cell_base + nlc;
+      const unsigned kb = c.key[gb];
+      const bool b_first = kb < kc || (kb == kc && gb < g);
+      if (in && b_first) ++deps;
+      if (out && !b_first) down |= 1u << f;
+    }
+    if (lane == 0) {
+      c.deps[g] = deps;
+      c.down[g] = down;
+    }
+  }
+}
+
+// Queue the cells that wait for nothing.
+__global__ void seed_ready_kernel(int total_cells, CellArrays c, Control* ctl) {
+  if (ctl->status) return;
+  unsigned long long pushes = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_cells;
+       g += gridDim.x * blockDim.x) {
+    if (c.deps[g] == 0) {
+      c.state[g] = kStQueued;
+      atomicAdd(&ctl->active, 1);
+      __threadfence();
+      queue_push(c, ctl, (unsigned)g, &pushes);
+    }
+  }
+  if (pushes) atomicAdd(&ctl->counters[1][kCntPushes], pushes);
+}
+
+__global__ void setup_polish_kernel(Control* ctl, int gated, double kappa) {
   if (threadIdx.x || blockIdx.x) return;
   if (ctl->status) return;
+  if (gated && !fallback_needed(ctl, kappa)) return;
   const double umax = double_of_ord(ctl->umax_bits);
   double width = 1.0 / (double)ctl->inv_width;
   const double span = umax - (double)ctl->base;
@@ -250,8 +414,10 @@ __global__ void setup_polish_kernel(Control* ctl) {
 }
 
 // Queue every cell for the polish.
-__global__ void seed_all_kernel(int total_cells, CellArrays c, Control* ctl) {
+__global__ void seed_all_kernel(int total_cells, CellArrays c, Control* ctl, int pass, int gated,
+                                double kappa) {
   if (ctl->status) return;
+  if (gated && !fallback_needed(ctl, kappa)) return;
   unsigned long long pushes = 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_cells;
        g += gridDim.x * blockDim.x) {
@@ -260,16 +426,18 @@ __global__ void seed_all_kernel(int total_cells, CellArrays c, Control* ctl) {
     __threadfence();
     queue_push(c, ctl, (unsigned)g, &pushes);
   }
-  if (pushes) atomicAdd(&ctl->counters[1][kCntPushes], pushes);
+  if (pushes) atomicAdd(&ctl->counters[pass][kCntPushes], pushes);
 }
 
 // max |u - Lambda(u)| over non-exit grid nodes (FP64), count of non-finite
 // values, largest finite value; then copy-out to the caller's layout.
+template <bool FINAL>
 __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, int count,
                                         Control* ctl) {
   const int ii = blockIdx.y;
   if (ii >= count) return;
   const FinalInstance P = fi[ii];
+  const double qb = q_base(ctl);
   const double* u = static_cast<const double*>(P.u64);
   const double* s = static_cast<const double*>(P.s64);
   const int N = P.n, N3 = N * N * N;
@@ -281,7 +449,7 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, in
     const long long i = e % P.nx, j = (e / P.nx) % P.ny, k = e / ((long long)P.nx * P.ny);
     const long long t = (i + 1) + sy * (j + 1) + sz * (k + 1);
     const double v = u[t];
-    P.out[e] = v;
+    if (FINAL) P.out[e] = P.mask[e] ? P.q[e] : v + qb;
     if (!isfinite(v)) {
       ++nbad;
       continue;
@@ -292,17 +460,21 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, in
     const long long lc = cx + P.ncx * (cy + (long long)P.ncy * cz);
     const double sv = s[lc * N3 + (i % N) + N * ((j % N) + N * (k % N))];
     if (!(sv < CUDART_INF)) continue;  // exit node
-    const double ax = fmin(u[t - 1], u[t + 1]);
-    const double ay = fmin(u[t - sy], u[t + sy]);
-    const double az = fmin(u[t - sz], u[t + sz]);
-    const double r = fabs(v - local_solve(ax, ay, az, sv));
+    const double ax = nmin(u[t - 1], u[t + 1]);
+    const double ay = nmin(u[t - sy], u[t + sy]);
+    const double az = nmin(u[t - sz], u[t + sz]);
+    const double lam = local_solve_direct(ax, ay, az, sv);
+    // final pass: |u - Lambda(u)|; check pass: how far u sits below Lambda(u)
+    const double r = FINAL ? fabs(v - lam) : fmax(lam - v, 0.0);
     const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
     rmax = rb > rmax ? rb : rmax;
   }
-  block_max_u64(rmax, &ctl->resid_bits);
-  block_max_u64(umax, &ctl->umax_bits);
-  for (int o = 16; o; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
-  if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(&ctl->nonfinite, nbad);
+  block_max_u64(rmax, FINAL ? &ctl->resid_bits : &ctl->check_bits);
+  if (FINAL) {
+    block_max_u64(umax, &ctl->final_umax_bits);
+    for (int o = 16; o; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+    if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(&ctl->nonfinite, nbad);
+  }
 }
 
 }  // namespace
@@ -318,45 +490,66 @@ static dim3 stream_grid(long long work, int count, int sms) {
 }
 
 cudaError_t launch_bulk_init(const PrepInstance* d_pi, int count, long long max_padded,
-                             long long max_cellnodes, int max_cells, int total_cells,
-                             CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
-                             double width_factor, int sms, cudaStream_t st) {
+                             long long max_cellnodes, long long max_nodes, int max_cells,
+                             int total_cells, CellArrays cells, Control* ctl, int* n_src, bool fp64,
+                             int n, double width_factor, double kappa_rel, int sms,
+                             cudaStream_t st) {
   reset_cells_kernel<float><<<stream_grid(max_cells, count, sms), 256, 0, st>>>(d_pi, count, cells);
+  minq_kernel<<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_pi, count, ctl, n_src);
   if (fp64) {
-    init_u_kernel<double><<<stream_grid(max_padded, count, sms), 256, 0, st>>>(d_pi, count);
+    init_u_kernel<double><<<stream_grid(max_padded, count, sms), 256, 0, st>>>(d_pi, count, ctl);
     init_s_kernel<double>
-        <<<stream_grid(max_cellnodes, count, sms), 256, 0, st>>>(d_pi, count, cells, ctl, n_src);
+        <<<stream_grid(max_cellnodes, count, sms), 256, 0, st>>>(d_pi, count, cells, ctl);
   } else {
-    init_u_kernel<float><<<stream_grid(max_padded, count, sms), 256, 0, st>>>(d_pi, count);
+    init_u_kernel<float><<<stream_grid(max_padded, count, sms), 256, 0, st>>>(d_pi, count, ctl);
     init_s_kernel<float>
-        <<<stream_grid(max_cellnodes, count, sms), 256, 0, st>>>(d_pi, count, cells, ctl, n_src);
+        <<<stream_grid(max_cellnodes, count, sms), 256, 0, st>>>(d_pi, count, cells, ctl);
   }
-  setup_bulk_kernel<<<1, 32, 0, st>>>(ctl, n_src, count, n, width_factor);
+  setup_bulk_kernel<<<1, 32, 0, st>>>(ctl, n_src, count, n, width_factor, kappa_rel);
   seed_sources_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells,
-                                                                            ctl);
+                                                                            ctl, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_polish_prep(const PolishInstance* d_pi, int count, long long max_padded64,
-                               int max_cells, int total_cells, CellArrays cells, Control* ctl,
-                               int sms, cudaStream_t st) {
+                               long long max_nodes, int max_cells, int total_cells,
+                               CellArrays cells, Control* ctl, int sms, cudaStream_t st) {
   convert_u_kernel<<<stream_grid(max_padded64, count, sms), 256, 0, st>>>(d_pi, count, ctl);
+  long long blocks = ((long long)max_cells * 32 + 255) / 256;
+  if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+  if (blocks < 1) blocks = 1;
+  polish_keys_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count, cells,
+                                                                            ctl, 0, 0.0);
+  polish_graph_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count, cells);
+  setup_polish_kernel<<<1, 32, 0, st>>>(ctl, 0, 0.0);
+  seed_ready_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells,
+                                                                          ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi, int count,
+                                 long long max_nodes, int max_cells, int total_cells,
+                                 CellArrays cells, Control* ctl, double kappa, int sms,
+                                 cudaStream_t st) {
+  residual_extract_kernel<false><<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_fi, count,
+                                                                                    ctl);
   {
-    long long warps = max_cells;
-    long long blocks = (warps * 32 + 255) / 256;
+    long long blocks = ((long long)max_cells * 32 + 255) / 256;
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
     if (blocks < 1) blocks = 1;
-    polish_keys_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count,
-                                                                              cells);
+    polish_keys_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count, cells,
+                                                                              ctl, 1, kappa);
   }
-  setup_polish_kernel<<<1, 32, 0, st>>>(ctl);
-  seed_all_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells, ctl);
+  setup_polish_kernel<<<1, 32, 0, st>>>(ctl, 1, kappa);
+  seed_all_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells, ctl,
+                                                                        2, 1, kappa);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_nodes,
                                     Control* ctl, int sms, cudaStream_t st) {
-  residual_extract_kernel<<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_fi, count, ctl);
+  residual_extract_kernel<true><<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_fi, count,
+                                                                                   ctl);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,8 @@ struct PolishInstance {
 
 // Residual check and copy-out of one instance.
 struct FinalInstance {
+  const uint8_t* mask;   // exit nodes are copied out as q exactly
+  const double* q;
   const void* u64;
   const void* s64;
   double* out;
@@ -47,12 +49,17 @@ struct FinalInstance {
 };
 
 cudaError_t launch_bulk_init(const PrepInstance* d_pi, int count, long long max_padded,
-                             long long max_cellnodes, int max_cells, int total_cells,
-                             CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
-                             double width_factor, int sms, cudaStream_t st);
+                             long long max_cellnodes, long long max_nodes, int max_cells,
+                             int total_cells, CellArrays cells, Control* ctl, int* n_src, bool fp64,
+                             int n, double width_factor, double kappa_rel, int sms,
+                             cudaStream_t st);
 cudaError_t launch_polish_prep(const PolishInstance* d_pi, int count, long long max_padded64,
-                               int max_cells, int total_cells, CellArrays cells, Control* ctl,
-                               int sms, cudaStream_t st);
+                               long long max_nodes, int max_cells, int total_cells,
+                               CellArrays cells, Control* ctl, int sms, cudaStream_t st);
+cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi, int count,
+                                 long long max_nodes, int max_cells, int total_cells,
+                                 CellArrays cells, Control* ctl, double kappa, int sms,
+                                 cudaStream_t st);
 cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_nodes,
                                     Control* ctl, int sms, cudaStream_t st);
 

@@ -37,12 +37,13 @@ EXPORTED = ("eik_opts_default", "eik_create", "eik_destroy", "eik_strerror",
 
 class Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int),
-                ("cell_n", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("cell_n", ctypes.c_int), ("max_ctas", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t),
                 ("spin_cap_us", ctypes.c_uint64),
                 ("bucket_width", ctypes.c_double),
                 ("max_sweeps_per_visit", ctypes.c_int),
-                ("reserved2", ctypes.c_int)]
+                ("queue_order", ctypes.c_int),
+                ("bulk_kappa_rel", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -57,10 +58,22 @@ class Stats(ctypes.Structure):
                 ("cell_n_used", ctypes.c_int), ("precision_used", ctypes.c_int),
                 ("residual_max", ctypes.c_double), ("u_max", ctypes.c_double),
                 ("seconds_bulk", ctypes.c_double),
-                ("seconds_polish", ctypes.c_double)]
+                ("seconds_polish", ctypes.c_double),
+                ("kernel_launches", ctypes.c_uint64),
+                ("grid_ctas", ctypes.c_int), ("fallback_used", ctypes.c_int),
+                ("busy_seconds_bulk", ctypes.c_double),
+                ("busy_seconds_polish", ctypes.c_double),
+                ("fallback_visits", ctypes.c_uint64),
+                ("phase_seconds", (ctypes.c_double * 4) * 2)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if name == "phase_seconds":
+                v = [[v[i][j] for j in range(4)] for i in range(2)]
+            d[name] = v
+        return d
 
 
 class EikError(RuntimeError):
@@ -144,12 +157,15 @@ class Solver:
 
     def __init__(self, precision="fp32_polish", cell_n=0, device=0,
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
-                 max_sweeps_per_visit=None):
+                 max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
+                 queue_order=0):
         self.lib = load()
         o = default_opts()
         o.device = device
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.cell_n = int(cell_n)
+        o.max_ctas = int(max_ctas)
+        o.queue_order = int(queue_order)
         o.hbm_budget_bytes = int(hbm_budget_bytes)
         if spin_cap_us is not None:
             o.spin_cap_us = int(spin_cap_us)
@@ -157,6 +173,8 @@ class Solver:
             o.bucket_width = float(bucket_width)
         if max_sweeps_per_visit is not None:
             o.max_sweeps_per_visit = int(max_sweeps_per_visit)
+        if bulk_kappa_rel is not None:
+            o.bulk_kappa_rel = float(bulk_kappa_rel)
         self.opts = o
         self.ctx = ctypes.c_void_p()
         rc = self.lib.eik_create(ctypes.byref(self.ctx), ctypes.byref(o))

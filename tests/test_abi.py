@@ -34,7 +34,7 @@ def test_defaults_and_strerror_without_gpu():
     from paper_1306_4743_gb300 import eik
     o = eik.default_opts()
     assert o.precision == 1 and o.cell_n == 0 and o.spin_cap_us == 5_000_000
-    assert o.max_sweeps_per_visit == 4096 and o.bucket_width == 1.0
+    assert o.max_sweeps_per_visit == 4096 and o.bucket_width == 0.5 and o.queue_order == 1
     lib = eik.load()
     assert lib.eik_strerror(0) == b"ok"
     assert lib.eik_strerror(5).startswith(b"device wait")

@@ -1,0 +1,126 @@
+"""Entry points and failure paths of the C ABI on the GPU: device-buffer
+solves, batches, queue orders, the memory budget, the device wait limit,
+and reuse of a context after an error."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_4743_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32_polish": 1e-9}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def eik(torch):
+    from paper_1306_4743_gb300 import eik as e
+    e.load()
+    return e
+
+
+def rel_err(u, p):
+    ref = oracle.fmm(p.F, p.mask, p.q, p.h)
+    return float(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("bw", [0.25, 2.0])
+def test_queue_orders_and_bucket_widths(eik, precision, order, bw):
+    p = W.oscillatory(73, amp=0.5)
+    with eik.Solver(precision=precision, cell_n=8, queue_order=order, bucket_width=bw) as s:
+        u, st = s.solve(p.F, p.mask, p.q, p.h)
+    assert rel_err(u, p) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
+def test_device_buffers_match_host_buffers(eik, torch, precision):
+    p = W.gaussian_bumps((45, 38, 29), seed=17)
+    with eik.Solver(precision=precision, cell_n=8) as s:
+        u_h, _ = s.solve(p.F, p.mask, p.q, p.h)
+        dev = torch.device("cuda", 0)
+        u_d, st = s.solve(torch.from_numpy(p.F).to(dev), torch.from_numpy(p.mask).to(dev),
+                          torch.from_numpy(p.q).to(dev), p.h)
+    assert rel_err(u_h, p) <= TOL[precision]
+    assert rel_err(u_d.cpu().numpy(), p) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
+def test_batch_matches_single_solves(eik, precision):
+    probs = [W.gaussian_bumps(d, 4000 + k) for k, d in
+             enumerate([(33, 65, 33), (65, 33, 33), (33, 33, 33), (41, 27, 19), (9, 9, 9)])]
+    with eik.Solver(precision=precision, cell_n=8) as s:
+        outs, st = s.solve_batch([(p.F, p.mask, p.q, p.h) for p in probs])
+    assert st["nodes"] == sum(p.nodes for p in probs)
+    for u, p in zip(outs, probs):
+        assert rel_err(u, p) <= TOL[precision]
+        assert np.array_equal(u[p.mask == 1], p.q[p.mask == 1])
+
+
+def test_negative_and_mixed_exit_values(eik):
+    rng = np.random.default_rng(3)
+    F = rng.uniform(0.5, 1.5, (20, 24, 28)).astype(np.float32)
+    mask = np.zeros(F.shape, np.uint8)
+    q = np.zeros(F.shape)
+    for t, v in zip(rng.choice(F.size, 5, replace=False), [-3.0, -2.5, 0.1, 1.0, -2.9]):
+        mask.reshape(-1)[t] = 1
+        q.reshape(-1)[t] = v
+    p = W.Problem(F, mask, q, 0.05)
+    for precision in ("fp64", "fp32_polish"):
+        with eik.Solver(precision=precision, cell_n=8) as s:
+            u, _ = s.solve(p.F, p.mask, p.q, p.h)
+        ref = oracle.fmm(p.F, p.mask, p.q, p.h)
+        assert np.max(np.abs(u - ref)) <= TOL[precision] * np.max(np.abs(ref))
+        assert np.array_equal(u[mask == 1], q[mask == 1])
+
+
+def test_budget_is_enforced(eik):
+    p = W.point_source_const(33)
+    with eik.Solver(precision="fp64", hbm_budget_bytes=1 << 16) as s:
+        _, st = s.solve(p.F, p.mask, p.q, p.h, check=False)
+        assert st["status"] == 3  # EIK_EBUDGET
+
+
+def test_wait_limit_returns_timeout_and_context_recovers(eik):
+    # spin_cap_us = 0: the first idle wait of any worker gives up at once;
+    # the kernel ends with EIK_ETIMEOUT instead of waiting
+    p = W.point_source_const(41)
+    with eik.Solver(precision="fp64", cell_n=8, spin_cap_us=0) as s:
+        _, st = s.solve(p.F, p.mask, p.q, p.h, check=False)
+        assert st["status"] == 5
+    # a fresh context on the same device still solves correctly
+    with eik.Solver(precision="fp64", cell_n=8) as s:
+        u, st = s.solve(p.F, p.mask, p.q, p.h)
+    assert rel_err(u, p) <= 1e-10
+
+
+def test_context_reuse_across_sizes(eik):
+    with eik.Solver(precision="fp32_polish") as s:
+        for m in (17, 65, 33, 129, 9):
+            p = W.oscillatory(m)
+            u, st = s.solve(p.F, p.mask, p.q, p.h)
+            assert rel_err(u, p) <= 1e-9
+            assert st["cell_n_used"] == (16 if p.nodes >= 2 ** 21 else 8)
+
+
+def test_stats_are_consistent(eik):
+    p = W.oscillatory(65)
+    with eik.Solver(precision="fp32_polish", cell_n=8) as s:
+        u, st = s.solve(p.F, p.mask, p.q, p.h)
+    assert st["nodes"] == p.nodes and st["nonfinite"] == 0
+    assert st["cell_visits"] >= (65 // 8 + 1) ** 3 // 2
+    assert st["sweeps"] >= st["cell_visits"] and st["polish_sweeps"] >= st["polish_visits"]
+    assert st["node_updates"] > 0 and st["polish_node_updates"] > 0
+    assert 0 < st["seconds_bulk"] < st["seconds"] and 0 < st["seconds_polish"] < st["seconds"]
+    assert st["residual_max"] <= 1e-14 * st["u_max"]
+    assert abs(st["u_max"] - u.max()) <= 1e-15 * u.max()
+    assert st["kernel_launches"] > 0 and st["grid_ctas"] > 0

@@ -207,6 +207,43 @@ int eik_submit(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
 int eik_poll(eik_ctx *ctx, uint64_t ticket, int *done, eik_stats *stats);
 int eik_cancel(eik_ctx *ctx, uint64_t ticket);
 
+/*
+ * Allocation-free FP64 solve (this entry point has no counterpart in the
+ * paper; it exists for the callers below).
+ *
+ * Some callers cannot allocate device memory while they solve: code that
+ * runs while another framework is capturing a CUDA graph (cudaMalloc is not
+ * allowed inside a capture), programs whose own allocator owns all device
+ * memory, and latency-critical loops where an allocation may stall on a
+ * device-wide synchronisation.  eik_solve_device_noalloc needs no context and
+ * calls no allocating routine: its working memory is one fixed device array
+ * of EIK_NOALLOC_SCRATCH_BYTES inside the library, which every device that
+ * loads the library holds until the process exits.
+ *
+ * Arguments as eik_solve_device (device buffers on the current device,
+ * stream = cudaStream_t or NULL); the sweeps run in FP64 with cells of 8^3
+ * nodes.  The call returns after the stream has finished the solve; stats
+ * (may be NULL) gets the counters and the residual, not the timings.
+ *
+ * Limits and sharing:
+ *  - a grid needs about 17 bytes of scratch per node plus padding; larger
+ *    grids (above roughly 150^3 nodes for a cube) are rejected with
+ *    EIK_EBUDGET before any device work;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - all calls share the one array (per device), and the array keeps the
+ *    last call's contents; a call initialises everything it reads, but two
+ *    calls whose device work overlaps (different streams, or host threads)
+ *    race on the array and give wrong results.  Calls from several host
+ *    threads are serialised on the host.
+ */
+#define EIK_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int eik_solve_device_noalloc(const int64_t dims[3], double h, const float *F_dev,
+                             const uint8_t *src_mask_dev, const double *q_dev,
+                             double tol, double *u_out_dev, void *stream,
+                             eik_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,8 @@ PRECISIONS = {"fp64": 0, "fp32_polish": 1}
 # Every C entry point declared in include/eik.h.
 EXPORTED = ("eik_opts_default", "eik_create", "eik_destroy", "eik_strerror",
             "eik_solve", "eik_solve_device", "eik_solve_batch",
-            "eik_solve_batch_device", "eik_submit", "eik_poll", "eik_cancel")
+            "eik_solve_batch_device", "eik_submit", "eik_poll", "eik_cancel",
+            "eik_solve_device_noalloc")
 
 
 class Opts(ctypes.Structure):
@@ -118,6 +119,7 @@ def load(path: str | None = None):
     lib.eik_submit.argtypes = [P, P, D, P, P, P, D, P, ctypes.POINTER(ctypes.c_uint64)]
     lib.eik_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(Stats)]
     lib.eik_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.eik_solve_device_noalloc.argtypes = [P, D, P, P, P, D, P, P, ctypes.POINTER(Stats)]
     for name in EXPORTED:
         if name != "eik_strerror":
             getattr(lib, name).restype = I

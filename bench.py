@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path and batch comparison lines")
+    ap.add_argument("--tol", type=float, default=1e-12,
+                    help="kappa of the FP64 sweeps (early-termination threshold)")
     return ap.parse_args()
 
 
@@ -216,7 +218,7 @@ def run_ours(args):
 
     solver = eik.Solver(precision=args.precision, cell_n=args.cell_n, device=local)
     for _ in range(args.warmup):
-        solver.solve(F_d, m_d, q_d, p.h, tol=0.0, out=u_d)
+        solver.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u_d)
     torch.cuda.synchronize(dev)
 
     def barrier():
@@ -235,7 +237,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = solver.solve(F_d, m_d, q_d, p.h, tol=0.0, out=u_d)
+        _, st = solver.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u_d)
         e1.record(stream)
         e1.synchronize()
         ev_ms.append(e0.elapsed_time(e1))
@@ -261,13 +263,13 @@ def run_ours(args):
     u_h = torch.empty(p.F.shape, dtype=torch.float64).pin_memory()
     Fn, mn, qn, un = F_h.numpy(), m_h.numpy(), q_h.numpy(), u_h.numpy()
     e2e_steps = max(3, min(args.steps, 10))
-    solver.solve(Fn, mn, qn, p.h, out=un)
+    solver.solve(Fn, mn, qn, p.h, tol=args.tol, out=un)
     e2e_t = []
     for _ in range(e2e_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        solver.solve(Fn, mn, qn, p.h, out=un)
+        solver.solve(Fn, mn, qn, p.h, tol=args.tol, out=un)
         e2e_t.append(time.perf_counter() - t0)
     e2e_value = world * p.nodes / statistics.mean(e2e_t)
     h2d = p.F.nbytes + p.mask.nbytes + p.q.nbytes
@@ -286,7 +288,7 @@ def run_ours(args):
                                   tb, vb, es_b)
         ktag = "bulk_f32" if es_b == 4 else "bulk_f64"
     else:
-        kname, ksec, kvis, kes = "cells_kernel<double,%d,replace>" % n, tp, vp, 8
+        kname, ksec, kvis, kes = "cells_kernel<double,%d> (FP64 polish)" % n, tp, vp, 8
         ktag = "polish_f64"
     bpv = bytes_per_visit(n, kes)
     achieved = kvis * bpv / ksec / 1e9
@@ -303,6 +305,7 @@ def run_ours(args):
     # parity of the timed result against the oracle, and the CPU baseline
     cpu = None
     err_rel = None
+    ref = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
@@ -316,16 +319,44 @@ def run_ours(args):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        # single-instance FP64 path on the same grid
+        # the plain single-instance FP64 path on the same grid
+        u64 = torch.empty_like(u_d)
         with eik.Solver(precision="fp64", cell_n=args.cell_n, device=local) as s64:
-            s64.solve(F_d, m_d, q_d, p.h, out=u_d)
+            s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
             ts = []
             for _ in range(3):
                 flush.fill_(1.0)
-                _, st = s64.solve(F_d, m_d, q_d, p.h, out=u_d)
+                _, st = s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
                 ts.append(st["seconds"])
-            extras["fp64_single_instance_nodes_per_s"] = p.nodes / statistics.mean(ts)
-            extras["fp64_single_instance_ms"] = statistics.mean(ts) * 1e3
+        extras["fp64_single_instance"] = {
+            "nodes_per_s": p.nodes / statistics.mean(ts), "ms": statistics.mean(ts) * 1e3,
+            "max_rel_err_vs_oracle": (float(np.max(np.abs(u64.cpu().numpy() - ref)) / np.max(ref))
+                                      if cpu is not None else None)}
+        # the batch of 256 uneven instances in one persistent launch
+        from paper_1306_4743_gb300 import workloads as W
+        probs = W.batch_instances(256)
+        bt = [(torch.from_numpy(b.F).to(dev), torch.from_numpy(b.mask).to(dev),
+               torch.from_numpy(b.q).to(dev), b.h) for b in probs]
+        bnodes = sum(b.nodes for b in probs)
+        with eik.Solver(precision=args.precision, device=local) as sb:
+            outs, st = sb.solve_batch_device(bt, tol=args.tol)
+            ts = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                outs, st = sb.solve_batch_device(bt, tol=args.tol, outs=outs)
+                ts.append(st["seconds"])
+        batch_err = None
+        if cpu is not None:
+            import oracle
+            errs = []
+            for k in (0, 100, 255):
+                r = oracle.fmm(probs[k].F, probs[k].mask, probs[k].q, probs[k].h)
+                errs.append(float(np.max(np.abs(outs[k].cpu().numpy() - r)) / np.max(r)))
+            batch_err = max(errs)
+        extras["batch256"] = {
+            "nodes": bnodes, "nodes_per_s": bnodes / statistics.mean(ts),
+            "ms": statistics.mean(ts) * 1e3, "cell_n": st["cell_n_used"],
+            "max_rel_err_vs_oracle_sampled_3": batch_err}
 
     out = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
@@ -334,7 +365,7 @@ def run_ours(args):
         "dtype": "f32+f64" if args.precision == "fp32_polish" else "f64",
         "data": "synthetic",
         "config": {"workload": workload_desc(args.edge, args.precision), "nodes": p.nodes,
-                   "cell_n": n, "precision": args.precision,
+                   "cell_n": n, "precision": args.precision, "tol": args.tol,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MB L2 flush between steps (outside the step events); the "
                          "solve's working set (~0.6 GB) also exceeds the 129 MB L2"},
@@ -349,6 +380,12 @@ def run_ours(args):
             "fp64": statistics.mean(s["polish_node_updates"] for s in stats) / tp if tp else None},
         "visits": {"bulk": vb, "polish": vp, "cells": int(math.ceil(args.edge / n) ** 3)},
         "max_rel_err_vs_oracle": err_rel,
+        # FP64 pipe view of the polish: ~14 FP64-pipe instructions per local
+        # solve (Newton-refined form), against 1.25 TFLOP/s / 2 = 0.625 T
+        # FP64 instructions/s nominal
+        "fp64_pipe_estimate": ({"instr_per_s": 14 * statistics.mean(
+            s["polish_node_updates"] for s in stats) / tp, "peak_instr_per_s": 0.625e12}
+            if tp else None),
         "residual_max": last["residual_max"],
         "bulk_ms": tb * 1e3, "polish_ms": tp * 1e3,
         "wall_s_timed_region": wall,

@@ -34,6 +34,10 @@ namespace eik {
 // (+++), (-++), (--+), (+-+), (++-), (-+-), (---), (+--).
 static __constant__ int kStdOrder[8] = {0, 1, 3, 2, 4, 5, 7, 6};
 
+// a < b for stored values (>= 0: the FP64 compare runs on the integer pipe)
+__device__ __forceinline__ bool vlt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool vlt(double a, double b) { return dlt_nn(a, b); }
+
 // Per-node bits of the staged cell: written back, changed by more than
 // kappa (flags the neighbour cell), active (to be recomputed, Alg. 2).
 constexpr unsigned char kWritten = 1, kBig = 2, kActive = 4;
@@ -96,11 +100,12 @@ __device__ __forceinline__ bool sweep_cell(T* __restrict__ U, const T* __restric
   bool changed = false;
   for (int C = 0; C < G::NPLANES; ++C) {
     const int beg = off[C], end = off[C + 1];
-    // Nodes of one plane do not depend on each other: each thread takes two
+    // Nodes of one plane do not depend on each other: each thread takes UNR
     // per pass, so their loads and arithmetic overlap.
-    for (int e0 = beg + tid; e0 < end; e0 += 2 * NT) {
+    constexpr int UNR = (N >= 16 && WPC == 1) ? 3 : 2;
+    for (int e0 = beg + tid; e0 < end; e0 += UNR * NT) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < UNR; ++h) {
         const int e = e0 + h * NT;
         if (e >= end) break;
         const unsigned pk = tab[e];
@@ -118,12 +123,14 @@ __device__ __forceinline__ bool sweep_cell(T* __restrict__ U, const T* __restric
           const T xm = U[t - 1], xp = U[t + 1];
           const T ym = U[t - G::SY], yp = U[t + G::SY];
           const T zm = U[t - G::SZ], zp = U[t + G::SZ];
+          const T vk = v - kappa;  // off the solve's dependency chain
           const T nv = local_solve(nmin(xm, xp), nmin(ym, yp), nmin(zm, zp), s);
           ++n_updates;
           bool big;
           if constexpr (!REPLACE) {
-            big = nv < v && v - nv > kappa;
-            if (nv < v) {
+            const bool lower = vlt(nv, v);
+            big = vlt(nv, vk);
+            if (lower) {
               U[t] = nv;
               c1 |= big ? 3 : 1;
             }
@@ -311,6 +318,20 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       const int nlim = axis == 0 ? I.ncx : axis == 1 ? I.ncy : I.ncz;
       unsigned m = 0xffffffffu;
       if (ncoord >= 0 && ncoord < nlim) {  // warp-uniform
+        // Polish: a neighbour cell not yet visited still holds its lifted
+        // start values V0 = U32 (1 + 2^-11); its fixed-point values are at
+        // most U32 (1 + 2^-15) (the FP32 error bound), so the border test
+        // compares with V0 scaled back to that bound instead of V0 itself.
+        T shrink = (T)1;
+        if (!REPLACE && p.gated) {
+          const int nlc = axis == 0 ? lc + (upper ? 1 : -1)
+                        : axis == 1 ? lc + (upper ? I.ncx : -I.ncx)
+                                    : lc + (upper ? I.ncx * I.ncy : -I.ncx * I.ncy);
+          unsigned vis = 0;
+          if (lane == 0) vis = ld_relaxed_u32(cells.down + I.cell_base + nlc) & 0x100u;
+          vis = __shfl_sync(0xffffffffu, vis, 0);
+          if (!vis) shrink = (T)0.99954229454883116;  // (1 + 2^-15) / (1 + 2^-11)
+        }
         for (int q = lane; q < N * N; q += 32) {
           const int a = q % N, b = q / N;
           int i, j, k;
@@ -321,7 +342,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
             const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
             const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
             const T vi = U[t];
-            const T vj = U[upper ? t + step : t - step];  // halo value
+            const T vj = U[upper ? t + step : t - step] * shrink;  // halo value
             // Min mode: only a border value below its neighbour's can be
             // used by the neighbour, and the (possibly stale) halo value is
             // never below the neighbour's current one, so this test misses

@@ -1,7 +1,8 @@
 // eik_cells_launch.cuh -- launch configuration of the persistent cell kernel
-// per (value type, cell size): workers of one warp for n <= 8, of four warps
-// for n = 16; grid = SM count x resident CTAs per SM (all CTAs co-resident,
-// as a persistent kernel needs).
+// per (value type, cell size): a worker is one warp for n <= 8 and four warps
+// for n = 16 (the sweep of one cell is on the critical path, so a 16^3 cell
+// gets more lanes per plane); grid = SM count x resident CTAs per SM, at
+// most two per SM by default.
 #pragma once
 #include "eik_cells.cuh"
 #include "eik_prep.h"

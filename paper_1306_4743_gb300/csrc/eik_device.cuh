@@ -219,15 +219,37 @@ __device__ __forceinline__ double local_solve_direct(double ax, double ay, doubl
   return a1 + (b + b3 + sqrt(fmax(d3, 0.0))) * 0.33333333333333331;
 }
 
+// double <-> float conversions on the integer pipe for values >= 0: the
+// conversion instructions take the FP64 path, whose latency (about 64 cycles
+// per dependent operation on this GPU) dominates the FP64 sweeps.  The
+// narrowing truncates the mantissa (relative error < 2^-23), which is all
+// the FP32 estimate below needs; values below the float range become 0,
+// above it +inf.
+__device__ __forceinline__ float f32_of_f64_nn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(b >> 52) - 896;
+  const unsigned r = ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffull);
+  return __uint_as_float(e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : r));
+}
+__device__ __forceinline__ double f64_of_f32_nn(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long e = u >> 23;
+  const unsigned long long r = ((e + 896ull) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double(
+      (long long)(e == 0 ? 0ull : (e == 255 ? 0x7ff0000000000000ull : r)));
+}
+__device__ __forceinline__ bool dlt_nn(double a, double b) { return dbits(a) < dbits(b); }
+
 // FP64 local solve used by the sweeps: the shifted root w = U - a1 of
 //   f(w) = sum_{d<=m} (w - b_d)^2 - s^2 = 0,   b_d = a_d - a1,
 // is first found in FP32 (term count m, and w32 to ~1e-7 relative), then
-// refined by one Newton step in FP64:  w = w32 - f(w32) / f'(w32), with
-// f'(w) = 2 sum_{d<=m} (w - b_d) >= 2w >= 2s/sqrt(3).  Newton's error after
-// one step is ~ m e0^2 / f', i.e. ~1e-14 s, below an FP64 ulp of U; f' only
-// scales the tiny correction, so it is taken in FP32.  The one-term root is
-// exact (U = a1 + s).  Near a branch boundary the m-term roots of both
-// branches agree to O(e0^2 / s), so the FP32 choice of m costs nothing.
+// refined by one Newton step in FP64:  U = (a1 + w32) - f(w32) / f'(w32),
+// with f'(w) = 2 sum_{d<=m} (w - b_d) >= 2w >= 2s/sqrt(3).  Newton's error
+// after one step is ~ m e0^2 / f', i.e. ~1e-14 s, below an FP64 ulp of U;
+// f' only scales the tiny correction, so 1/f' is taken in FP32.  The
+// one-term root is exact (U = a1 + s).  Near a branch boundary the m-term
+// roots of both branches agree to O(e0^2 / s), so the FP32 choice of m
+// costs nothing.  The FP64 part is four dependent operations deep.
 __device__ __forceinline__ double local_solve(double ax, double ay, double az, double s) {
   const double lo = dmin_nn(ax, ay), hi = dmax_nn(ax, ay);
   const double a1 = dmin_nn(lo, az), mid = dmax_nn(lo, az);
@@ -235,23 +257,25 @@ __device__ __forceinline__ double local_solve(double ax, double ay, double az, d
   const double u1 = a1 + s;
   if (dle_nn(u1, a2)) return u1;  // one term, exact; also a1 = +inf
   const double b2 = a2 - a1, b3 = a3 - a1;
-  const float fs = (float)s, fb2 = (float)b2, fb3 = (float)b3;
-  const float fs2 = fs * fs;
-  const float w2 = 0.5f * (fb2 + sqrtf(fmaxf(2.0f * fs2 - fb2 * fb2, 0.0f)));
   const double s2 = s * s;
+  const float fs = f32_of_f64_nn(s), fb2 = f32_of_f64_nn(b2), fb3 = f32_of_f64_nn(b3);
+  const float fs2 = fs * fs;
+  const float w2 = 0.5f * (fb2 + sqrt_fast(fmaxf(2.0f * fs2 - fb2 * fb2, 0.0f)));
   if (w2 <= fb3) {
-    const double w = (double)w2, r2 = w - b2;
-    const double f = fma(w, w, fma(r2, r2, -s2));
-    const float rinv = 0.5f / (2.0f * w2 - fb2);
-    return a1 + (w - f * (double)rinv);
+    const double w = f64_of_f32_nn(w2);
+    const double r2 = w - b2, t = fma(w, w, -s2), a1w = a1 + w;
+    const double f = fma(r2, r2, t);
+    const double rinv = f64_of_f32_nn(__fdividef(0.5f, 2.0f * w2 - fb2));
+    return fma(-f, rinv, a1w);
   }
   const float e = fb3 - fb2;
   const float d3 = 3.0f * fs2 - (fb2 * fb2 + fb3 * fb3 + e * e);
-  const float w3 = (fb2 + fb3 + sqrtf(fmaxf(d3, 0.0f))) * (1.0f / 3.0f);
-  const double w = (double)w3, r2 = w - b2, r3 = w - b3;
-  const double f = fma(w, w, fma(r2, r2, fma(r3, r3, -s2)));
-  const float rinv = 0.5f / (3.0f * w3 - fb2 - fb3);
-  return a1 + (w - f * (double)rinv);
+  const float w3 = (fb2 + fb3 + sqrt_fast(fmaxf(d3, 0.0f))) * (1.0f / 3.0f);
+  const double w = f64_of_f32_nn(w3);
+  const double r2 = w - b2, r3 = w - b3, t = fma(w, w, -s2), a1w = a1 + w;
+  const double f = fma(r3, r3, fma(r2, r2, t));
+  const double rinv = f64_of_f32_nn(__fdividef(0.5f, 3.0f * w3 - fb2 - fb3));
+  return fma(-f, rinv, a1w);
 }
 
 // Axis minimum of two neighbour values.

@@ -259,7 +259,7 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, int coun
 __device__ __forceinline__ bool fallback_needed(const Control* ctl, double kappa) {
   const double check = __longlong_as_double((long long)ctl->check_bits);
   const double umax = double_of_ord(ctl->umax_bits);
-  return check > kappa + 1e-13 * fmax(fabs(umax), 1.0);
+  return check > 4.0 * kappa + 1e-13 * fmax(fabs(umax), 1.0);
 }
 
 __global__ void polish_keys_kernel(const PolishInstance* __restrict__ pi, int count,
@@ -464,8 +464,10 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, in
     const double ay = nmin(u[t - sy], u[t + sy]);
     const double az = nmin(u[t - sz], u[t + sz]);
     const double lam = local_solve_direct(ax, ay, az, sv);
-    // final pass: |u - Lambda(u)|; check pass: how far u sits below Lambda(u)
-    const double r = FINAL ? fabs(v - lam) : fmax(lam - v, 0.0);
+    // |u - Lambda(u)|: in the check pass, a value left below the fixed point
+    // (lift too small) or above it (a flag skipped on the FP32 error bound)
+    // both send the solve to the replace-mode fallback
+    const double r = fabs(v - lam);
     const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
     rmax = rb > rmax ? rb : rmax;
   }

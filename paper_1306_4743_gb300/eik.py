@@ -134,6 +134,30 @@ def default_opts() -> Opts:
     return o
 
 
+def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
+              spin_cap_us=None, bucket_width=None, max_sweeps_per_visit=None, max_ctas=0,
+              bulk_kappa_rel=None, queue_order=None) -> Opts:
+    """eik_opts from the library defaults with the given fields changed
+    (None = keep the default)."""
+    o = default_opts()
+    o.device = int(device)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.cell_n = int(cell_n)
+    o.max_ctas = int(max_ctas)
+    o.hbm_budget_bytes = int(hbm_budget_bytes)
+    if spin_cap_us is not None:
+        o.spin_cap_us = int(spin_cap_us)
+    if bucket_width is not None:
+        o.bucket_width = float(bucket_width)
+    if max_sweeps_per_visit is not None:
+        o.max_sweeps_per_visit = int(max_sweeps_per_visit)
+    if bulk_kappa_rel is not None:
+        o.bulk_kappa_rel = float(bulk_kappa_rel)
+    if queue_order is not None:
+        o.queue_order = int(queue_order)
+    return o
+
+
 def _host_arrays(F, mask, q):
     F = np.ascontiguousarray(F, dtype=np.float32)
     if F.ndim != 3:
@@ -160,23 +184,14 @@ class Solver:
     def __init__(self, precision="fp32_polish", cell_n=0, device=0,
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
                  max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
-                 queue_order=0):
+                 queue_order=None):
+        """Options left at None keep the library defaults (eik_opts_default)."""
         self.lib = load()
-        o = default_opts()
-        o.device = device
-        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        o.cell_n = int(cell_n)
-        o.max_ctas = int(max_ctas)
-        o.queue_order = int(queue_order)
-        o.hbm_budget_bytes = int(hbm_budget_bytes)
-        if spin_cap_us is not None:
-            o.spin_cap_us = int(spin_cap_us)
-        if bucket_width is not None:
-            o.bucket_width = float(bucket_width)
-        if max_sweeps_per_visit is not None:
-            o.max_sweeps_per_visit = int(max_sweeps_per_visit)
-        if bulk_kappa_rel is not None:
-            o.bulk_kappa_rel = float(bulk_kappa_rel)
+        o = make_opts(precision=precision, cell_n=cell_n, device=device,
+                      hbm_budget_bytes=hbm_budget_bytes, spin_cap_us=spin_cap_us,
+                      bucket_width=bucket_width, max_sweeps_per_visit=max_sweeps_per_visit,
+                      max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
+                      queue_order=queue_order)
         self.opts = o
         self.ctx = ctypes.c_void_p()
         rc = self.lib.eik_create(ctypes.byref(self.ctx), ctypes.byref(o))

@@ -62,3 +62,14 @@ def test_invalid_options_rejected_before_device_use():
     o.precision = 7
     assert lib.eik_create(ctypes.byref(ctx), ctypes.byref(o)) == 1
     assert not ctx
+
+
+def test_binding_keeps_library_defaults():
+    from paper_1306_4743_gb300 import eik
+    d = eik.default_opts()
+    o = eik.make_opts()
+    for name, _ in eik.Opts._fields_:
+        assert getattr(o, name) == getattr(d, name), name
+    o = eik.make_opts(precision="fp64", cell_n=16, queue_order=0, bucket_width=2.0)
+    assert (o.precision, o.cell_n, o.queue_order, o.bucket_width) == (0, 16, 0, 2.0)
+    assert o.bulk_kappa_rel == d.bulk_kappa_rel and o.spin_cap_us == d.spin_cap_us

@@ -48,16 +48,11 @@ struct eik_ctx {
   int sms = 0;
   cudaStream_t stream = nullptr;
   EncodeTiledFn encode = nullptr;
-  // grow-only device arena
-  char* arena = nullptr;
-  size_t arena_size = 0;
+  // execution slot of the synchronous calls
+  Exec main;
   // plane tables, per cell size (index 0: n=4, 1: n=8, 2: n=16)
   unsigned short* d_tab[3] = {nullptr, nullptr, nullptr};
   int* d_off[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev[6] = {};
-  // host staging of small tables (pinned)
-  char* h_small = nullptr;
-  size_t h_small_size = 0;
   // serving
   ServeState* serve = nullptr;
   // autotune cache: log2(nodes) bucket -> cell size
@@ -209,39 +204,39 @@ void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, i
   L.total = L.small_end;
 }
 
-int ensure_arena(eik_ctx* ctx, size_t bytes) {
-  if (ctx->opts.hbm_budget_bytes && bytes > ctx->opts.hbm_budget_bytes) return EIK_EBUDGET;
-  if (bytes <= ctx->arena_size) return EIK_OK;
-  if (ctx->arena) {
-    cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->arena);
-    ctx->arena = nullptr;
-    ctx->arena_size = 0;
+int ensure_arena(Exec& ex, size_t bytes, size_t limit) {
+  if (limit && bytes > limit) return EIK_EBUDGET;
+  if (bytes <= ex.arena_size) return EIK_OK;
+  if (ex.arena) {
+    cudaStreamSynchronize(ex.stream);
+    cudaFree(ex.arena);
+    ex.arena = nullptr;
+    ex.arena_size = 0;
   }
   size_t want = align_up(bytes + bytes / 8, 1 << 20);
-  if (ctx->opts.hbm_budget_bytes && want > ctx->opts.hbm_budget_bytes) want = bytes;
-  if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
+  if (limit && want > limit) want = bytes;
+  if (cudaMalloc(&ex.arena, want) != cudaSuccess) {
     cudaGetLastError();
-    if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
+    if (cudaMalloc(&ex.arena, bytes) != cudaSuccess) {
       cudaGetLastError();
       return EIK_ENOMEM;
     }
     want = bytes;
   }
-  ctx->arena_size = want;
+  ex.arena_size = want;
   return EIK_OK;
 }
 
-int ensure_host_small(eik_ctx* ctx, size_t bytes) {
-  if (bytes <= ctx->h_small_size) return EIK_OK;
-  if (ctx->h_small) cudaFreeHost(ctx->h_small);
-  ctx->h_small = nullptr;
-  ctx->h_small_size = 0;
-  if (cudaMallocHost(&ctx->h_small, bytes) != cudaSuccess) {
+int ensure_pinned(char** buf, size_t* have, size_t bytes) {
+  if (bytes <= *have) return EIK_OK;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *have = 0;
+  if (cudaMallocHost(buf, bytes) != cudaSuccess) {
     cudaGetLastError();
     return EIK_ENOMEM;
   }
-  ctx->h_small_size = bytes;
+  *have = bytes;
   return EIK_OK;
 }
 
@@ -279,11 +274,11 @@ bool valid_dims(const int64_t* d) {
 }  // namespace
 
 // Launch sequence of one batched solve.  IO arrays are host pointers when
-// host_io, else device pointers.  Leaves results in u_out (host or device).
-int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
-                  const float* const* F, const uint8_t* const* mask, const double* const* q,
-                  double tol, double* const* u_out, bool host_io, cudaStream_t st,
-                  eik_stats* stats, int n_override) {
+// host_io, else device pointers.
+int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, const double* h,
+                     const float* const* F, const uint8_t* const* mask, const double* const* q,
+                     double tol, double* const* u_out, bool host_io, cudaStream_t st,
+                     bool async_out, Launch& Lr, size_t arena_limit, int n_override) {
   if (!ctx || count < 1 || !dims || !h || !F || !mask || !q || !u_out) return EIK_EINVAL;
   if (!(tol >= 0.0) || isinf(tol)) return EIK_EINVAL;
   long long nodes_total = 0, nodes_max = 0;
@@ -304,14 +299,32 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   LaunchPlan L;
   make_plan(L, count, dims, h, n, polish, host_io);
   if (L.total_cells > (1 << 30)) return EIK_EINVAL;
-  int rc = ensure_arena(ctx, L.total);
+  int rc = ensure_arena(ex, L.total, arena_limit);
   if (rc) return rc;
-  rc = ensure_host_small(ctx, L.small_end - L.small_begin);
+  rc = ensure_pinned(&ex.h_small, &ex.h_small_size, L.small_end - L.small_begin);
   if (rc) return rc;
-  char* A = ctx->arena;
+  Lr = Launch();
+  Lr.count = count;
+  Lr.n = n;
+  Lr.polish = polish;
+  Lr.host_io = host_io;
+  Lr.async_out = async_out && host_io;
+  Lr.nodes_total = nodes_total;
+  Lr.outs.assign(u_out, u_out + count);
+  if (Lr.async_out) {
+    size_t ob = 0;
+    for (int t = 0; t < count; ++t) {
+      Lr.out_off.push_back(ob);
+      Lr.out_nodes.push_back(L.inst[t].nodes);
+      ob += align_up((size_t)L.inst[t].nodes * 8, 256);
+    }
+    rc = ensure_pinned(&ex.h_out, &ex.h_out_size, ob);
+    if (rc) return rc;
+  }
+  char* A = ex.arena;
 
   // host-side small tables
-  char* hs = ctx->h_small;
+  char* hs = ex.h_small;
   memset(hs, 0, L.small_end - L.small_begin);
   auto hptr = [&](size_t off) { return hs + (off - L.small_begin); };
   Control* hctl = reinterpret_cast<Control*>(hptr(L.off_ctl));
@@ -435,7 +448,7 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   cells.down = reinterpret_cast<unsigned*>(A + L.off_down);
   Control* dctl = reinterpret_cast<Control*>(A + L.off_ctl);
 
-  CK(cudaEventRecord(ctx->ev[0], st));
+  CK(cudaEventRecord(ex.ev[0], st));
   double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 0.5;
   CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), count,
                       L.max_padded_b, L.max_cellnodes, L.max_nodes, L.max_cells, L.total_cells,
@@ -456,10 +469,10 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   p.kappa_from_ctl = polish ? 1 : 0;
   p.relaxed = ctx->opts.queue_order;
   p.gated = 0;
-  CK(cudaEventRecord(ctx->ev[1], st));
+  CK(cudaEventRecord(ex.ev[1], st));
   int grid_ctas = 0;
   CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas));
-  CK(cudaEventRecord(ctx->ev[2], st));
+  CK(cudaEventRecord(ex.ev[2], st));
   if (polish) {
     CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), count,
                           L.max_padded64, L.max_nodes, L.max_cells, L.total_cells, cells, dctl,
@@ -469,10 +482,10 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
     p.pass = 1;
     p.kappa_from_ctl = 0;
     p.gated = 1;
-    CK(cudaEventRecord(ctx->ev[3], st));
+    CK(cudaEventRecord(ex.ev[3], st));
     // monotone FP64 sweeps down from the lifted FP32 result
     CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr));
-    CK(cudaEventRecord(ctx->ev[4], st));
+    CK(cudaEventRecord(ex.ev[4], st));
     // fallback, gated on the device: if some u ended below the fixed point
     // (lift too small), polish again with replace-mode sweeps
     CK(launch_fallback_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol),
@@ -485,27 +498,41 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   }
   CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
                              L.max_nodes, dctl, ctx->sms, st));
-  CK(cudaEventRecord(ctx->ev[5], st));
+  CK(cudaEventRecord(ex.ev[5], st));
   Control* hres = hctl;  // reuse the pinned staging for the read-back
   CK(cudaMemcpyAsync(hres, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   if (host_io) {
     for (int t = 0; t < count; ++t) {
       const InstPlan& I = L.inst[t];
-      CK(cudaMemcpyAsync(u_out[t], A + I.off_out, (size_t)I.nodes * 8, cudaMemcpyDeviceToHost,
-                         st));
+      void* dst = Lr.async_out ? (void*)(ex.h_out + Lr.out_off[t]) : (void*)u_out[t];
+      CK(cudaMemcpyAsync(dst, A + I.off_out, (size_t)I.nodes * 8, cudaMemcpyDeviceToHost, st));
     }
   }
-  CK(cudaStreamSynchronize(st));
+  Lr.hres = hres;
+  Lr.grid = grid_ctas;
+  return EIK_OK;
+}
 
+int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
+  (void)ctx;
+  const Control* hres = Lr.hres;
+  const bool polish = Lr.polish;
+  const int n = Lr.n;
+  const int grid_ctas = Lr.grid;
+  const long long nodes_total = Lr.nodes_total;
+  if (Lr.async_out) {
+    for (int t = 0; t < Lr.count; ++t)
+      memcpy(Lr.outs[t], ex.h_out + Lr.out_off[t], (size_t)Lr.out_nodes[t] * 8);
+  }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+    cudaEventElapsedTime(&ms, ex.ev[0], ex.ev[5]);
     stats->seconds = ms * 1e-3;
-    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&ms, ex.ev[1], ex.ev[2]);
     stats->seconds_bulk = ms * 1e-3;
     if (polish) {
-      cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]);
+      cudaEventElapsedTime(&ms, ex.ev[3], ex.ev[4]);
       stats->seconds_polish = ms * 1e-3;
     }
     stats->cell_visits = hres->counters[0][kCntVisits];
@@ -551,6 +578,66 @@ int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
   if (hres->nonfinite) return EIK_ENOCONV;
   return EIK_OK;
 }
+
+int eik_run_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
+                  const float* const* F, const uint8_t* const* mask, const double* const* q,
+                  double tol, double* const* u_out, bool host_io, cudaStream_t st,
+                  eik_stats* stats, int n_override) {
+  if (!ctx) return EIK_EINVAL;
+  Launch L;
+  int rc = eik_launch_batch(ctx, ctx->main, count, dims, h, F, mask, q, tol, u_out, host_io, st,
+                            false, L, ctx->opts.hbm_budget_bytes, n_override);
+  if (rc) {
+    if (rc == EIK_ECUDA) cudaStreamSynchronize(st);
+    return rc;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return EIK_ECUDA;
+  }
+  return eik_finish_batch(ctx, ctx->main, L, stats);
+}
+
+size_t eik_plan_bytes(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
+                      bool host_io) {
+  long long nodes_max = 0;
+  for (int t = 0; t < count; ++t)
+    nodes_max = std::max(nodes_max, (long long)dims[3 * t] * dims[3 * t + 1] * dims[3 * t + 2]);
+  LaunchPlan L;
+  make_plan(L, count, dims, h, choose_cell_n(ctx, nodes_max),
+            ctx->opts.precision == EIK_FP32_POLISH, host_io);
+  return L.total;
+}
+
+namespace eik {
+int exec_init(Exec& e, bool own_stream) {
+  if (own_stream) {
+    if (cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return EIK_ECUDA;
+    }
+    e.own_stream = true;
+  }
+  for (int i = 0; i < 6; ++i) {
+    if (cudaEventCreate(&e.ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return EIK_ECUDA;
+    }
+  }
+  return EIK_OK;
+}
+void exec_free(Exec& e) {
+  if (e.stream) cudaStreamSynchronize(e.stream);
+  if (e.arena) cudaFree(e.arena);
+  if (e.h_small) cudaFreeHost(e.h_small);
+  if (e.h_out) cudaFreeHost(e.h_out);
+  for (int i = 0; i < 6; ++i)
+    if (e.ev[i]) cudaEventDestroy(e.ev[i]);
+  if (e.own_stream && e.stream) cudaStreamDestroy(e.stream);
+  cudaGetLastError();
+  e = Exec();
+}
+}  // namespace eik
 
 // ---------------------------------------------------------------------------
 // C ABI.
@@ -618,12 +705,10 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
     delete c;
     return EIK_ECUDA;
   }
-  for (int i = 0; i < 6; ++i) {
-    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
-      cudaGetLastError();
-      eik_destroy(c);
-      return EIK_ECUDA;
-    }
+  c->main.stream = c->stream;
+  if (exec_init(c->main, false) != EIK_OK) {
+    eik_destroy(c);
+    return EIK_ECUDA;
   }
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult qres;
@@ -644,14 +729,11 @@ int eik_destroy(eik_ctx* c) {
   cudaSetDevice(c->device);
   if (c->serve) serve_destroy(c->serve);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->arena) cudaFree(c->arena);
+  exec_free(c->main);
   for (int i = 0; i < 3; ++i) {
     if (c->d_tab[i]) cudaFree(c->d_tab[i]);
     if (c->d_off[i]) cudaFree(c->d_off[i]);
   }
-  for (int i = 0; i < 6; ++i)
-    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-  if (c->h_small) cudaFreeHost(c->h_small);
   if (c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -694,3 +776,4 @@ int eik_solve_batch_device(eik_ctx* ctx, int count, const int64_t* dims, const d
 }  // extern "C"
 
 eik::ServeState*& eik_serve_slot(eik_ctx* ctx) { return ctx->serve; }
+size_t eik_ctx_budget(eik_ctx* ctx) { return ctx->opts.hbm_budget_bytes; }

@@ -193,6 +193,7 @@ class Solver:
                       max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
                       queue_order=queue_order)
         self.opts = o
+        self._outputs = {}  # ticket -> output array, alive until done or cancelled
         self.ctx = ctypes.c_void_p()
         rc = self.lib.eik_create(ctypes.byref(self.ctx), ctypes.byref(o))
         if rc != EIK_OK:
@@ -200,8 +201,9 @@ class Solver:
 
     def close(self):
         if self.ctx:
-            self.lib.eik_destroy(self.ctx)
+            self.lib.eik_destroy(self.ctx)  # waits for batches still on the device
             self.ctx = ctypes.c_void_p()
+            self._outputs.clear()
 
     def __enter__(self):
         return self
@@ -299,15 +301,20 @@ class Solver:
 
     # -- serving ------------------------------------------------------------
     def submit(self, F, mask, q, h, tol=0.0, out=None):
-        """Queue one solve; returns (ticket, out array filled on completion)."""
+        """Queue one solve; returns (ticket, out array filled on completion).
+        The binding keeps the output array alive until the ticket is done or
+        cancelled (the library writes into it asynchronously)."""
         F_h, m_h, q_h = _host_arrays(F, mask, q)
         u = out if out is not None else np.empty(F_h.shape, dtype=np.float64)
+        if not (u.flags.c_contiguous and u.dtype == np.float64 and u.shape == F_h.shape):
+            raise ValueError("out must be a C-contiguous float64 array of F's shape")
         t = ctypes.c_uint64()
         rc = self.lib.eik_submit(self.ctx, _dims_of(F_h.shape), float(h), F_h.ctypes.data,
                                  m_h.ctypes.data, q_h.ctypes.data, float(tol), u.ctypes.data,
                                  ctypes.byref(t))
         if rc != EIK_OK:
             raise EikError(rc, "eik_submit")
+        self._outputs[t.value] = u
         return t.value, u
 
     def poll(self, ticket):
@@ -316,10 +323,15 @@ class Solver:
         st = Stats()
         rc = self.lib.eik_poll(self.ctx, ctypes.c_uint64(ticket), ctypes.byref(done),
                                ctypes.byref(st))
+        if done.value:
+            self._outputs.pop(ticket, None)
         return bool(done.value), rc, st.as_dict()
 
     def cancel(self, ticket):
-        return self.lib.eik_cancel(self.ctx, ctypes.c_uint64(ticket))
+        rc = self.lib.eik_cancel(self.ctx, ctypes.c_uint64(ticket))
+        if rc == EIK_OK:
+            self._outputs.pop(ticket, None)
+        return rc
 
 
 def solve(F, mask, q, h, tol=0.0, precision="fp32_polish", cell_n=0):

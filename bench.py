@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path and batch comparison lines")
+    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--serve-unique", type=int, default=24)
     ap.add_argument("--tol", type=float, default=1e-12,
                     help="kappa of the FP64 sweeps (early-termination threshold)")
     return ap.parse_args()
@@ -196,6 +198,65 @@ def run_reference(args):
     }))
 
 
+def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, check=True):
+    """Poisson arrivals of solves (cubic edge log-uniform in [33, 385], speed
+    fields from the Gaussian-bump family), continuous batching through
+    eik_submit / eik_poll under an HBM budget.  Returns latency percentiles
+    and throughput.  Requests cycle over `n_unique` generated problems (the
+    first draws of the same edge / seed stream) to bound host memory."""
+    import numpy as np
+    draws = W.serving_requests(n=n_requests, rate=1.0, seed=5)
+    uniq = [W.serving_problem(edge, seed) for (_, edge, seed) in draws[:n_unique]]
+    with eik.Solver(precision="fp32_polish", device=device,
+                    hbm_budget_bytes=int(budget_gb * (1 << 30))) as s:
+        # closed loop: everything at once, to size the open-loop rate
+        s.solve(uniq[0].F, uniq[0].mask, uniq[0].q, uniq[0].h, tol=tol)
+        t0 = time.perf_counter()
+        tickets = [s.submit(p.F, p.mask, p.q, p.h, tol=tol)[0] for p in uniq]
+        left = set(tickets)
+        while left:
+            for t in list(left):
+                if s.poll(t)[0]:
+                    left.discard(t)
+        closed = len(uniq) / (time.perf_counter() - t0)
+        rate = 0.7 * closed
+        arrivals = [a for (a, _, _) in W.serving_requests(n=n_requests, rate=rate, seed=5)]
+        lat, nodes, out = [], 0, {}
+        nxt = 0
+        t0 = time.perf_counter()
+        while len(lat) < n_requests:
+            now = time.perf_counter() - t0
+            while nxt < n_requests and arrivals[nxt] <= now:
+                p = uniq[nxt % n_unique]
+                t, u = s.submit(p.F, p.mask, p.q, p.h, tol=tol)
+                out[t] = (nxt, arrivals[nxt], u)
+                nxt += 1
+            for t in list(out):
+                ok, rc, _ = s.poll(t)
+                if ok:
+                    k, arr, u = out.pop(t)
+                    if rc != 0:
+                        raise RuntimeError("serving request %d failed: %d" % (k, rc))
+                    lat.append(time.perf_counter() - t0 - arr)
+                    nodes += uniq[k % n_unique].nodes
+                    if check and k < n_unique and uniq[k].nodes <= 129 ** 3 and k % 3 == 0:
+                        import oracle
+                        pr = uniq[k]
+                        ref = oracle.fmm(pr.F, pr.mask, pr.q, pr.h)
+                        e = float(np.max(np.abs(u - ref)) / np.max(ref))
+                        if e > 1e-9:
+                            raise RuntimeError("serving request %d error %.2e" % (k, e))
+            if not out and nxt < n_requests:
+                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.002)))
+        span = time.perf_counter() - t0
+    lat_ms = np.sort(np.array(lat)) * 1e3
+    return {"requests": n_requests, "unique_problems": n_unique,
+            "rate_per_s": rate, "closed_loop_per_s": closed,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "nodes_per_s": nodes / span, "budget_gb": budget_gb,
+            "edges": "cubic, round(exp(U[ln 33, ln 385])), seed 5; F: 8 Gaussian bumps, seed 5000+k"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -247,13 +308,16 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
 
-    t_step = statistics.mean(ev_ms) * 1e-3
-    t_max = t_step
-    if world > 1:
+    def max_over_ranks(x):
+        if world == 1:
+            return x
         import torch.distributed as dist
-        tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        tt = torch.tensor([x], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+        return float(tt.item())
+
+    t_step = statistics.mean(ev_ms) * 1e-3
+    t_max = max_over_ranks(t_step)
     value = world * p.nodes / t_max
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -271,7 +335,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         solver.solve(Fn, mn, qn, p.h, tol=args.tol, out=un)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * p.nodes / statistics.mean(e2e_t)
+    e2e_value = world * p.nodes / max_over_ranks(statistics.mean(e2e_t))
     h2d = p.F.nbytes + p.mask.nbytes + p.q.nbytes
     d2h = p.nodes * 8
 
@@ -318,8 +382,44 @@ def run_ours(args):
                          "%d cores" % (args.edge, tc, os.cpu_count() or 0)}
 
     extras = {}
+    if not args.no_extras:
+        # the batch of 256 uneven instances; under torchrun each rank solves
+        # its share (greedy by size, no collective decides the split)
+        from paper_1306_4743_gb300 import dispatch
+        from paper_1306_4743_gb300 import workloads as W
+        probs = W.batch_instances(256)
+        mine = dispatch.shard([b.nodes for b in probs], rank, world)
+        bt = [(torch.from_numpy(probs[k].F).to(dev), torch.from_numpy(probs[k].mask).to(dev),
+               torch.from_numpy(probs[k].q).to(dev), probs[k].h) for k in mine]
+        bnodes = sum(b.nodes for b in probs)
+        with eik.Solver(precision=args.precision, device=local) as sb:
+            outs, st = sb.solve_batch_device(bt, tol=args.tol)
+            ts = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                barrier()
+                outs, st = sb.solve_batch_device(bt, tol=args.tol, outs=outs)
+                ts.append(st["seconds"])
+        tbatch = max_over_ranks(statistics.mean(ts))
+        batch_err = None
+        if rank == 0 and cpu is not None:
+            import oracle
+            errs = []
+            for k in (0, 100, 255):
+                if k not in mine:
+                    continue
+                r = oracle.fmm(probs[k].F, probs[k].mask, probs[k].q, probs[k].h)
+                o = outs[mine.index(k)]
+                errs.append(float(np.max(np.abs(o.cpu().numpy() - r)) / np.max(r)))
+            batch_err = max(errs) if errs else None
+        extras["batch256"] = {
+            "nodes": bnodes, "nodes_per_s": bnodes / tbatch,
+            "ms": tbatch * 1e3, "cell_n": st["cell_n_used"], "ranks": world,
+            "instances_rank0": len(mine),
+            "max_rel_err_vs_oracle_sampled": batch_err}
+        del bt, outs
     if rank == 0 and not args.no_extras:
-        # the plain single-instance FP64 path on the same grid
+        # the plain single-instance FP64 path on the same grid (rank 0)
         u64 = torch.empty_like(u_d)
         with eik.Solver(precision="fp64", cell_n=args.cell_n, device=local) as s64:
             s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
@@ -332,31 +432,9 @@ def run_ours(args):
             "nodes_per_s": p.nodes / statistics.mean(ts), "ms": statistics.mean(ts) * 1e3,
             "max_rel_err_vs_oracle": (float(np.max(np.abs(u64.cpu().numpy() - ref)) / np.max(ref))
                                       if cpu is not None else None)}
-        # the batch of 256 uneven instances in one persistent launch
-        from paper_1306_4743_gb300 import workloads as W
-        probs = W.batch_instances(256)
-        bt = [(torch.from_numpy(b.F).to(dev), torch.from_numpy(b.mask).to(dev),
-               torch.from_numpy(b.q).to(dev), b.h) for b in probs]
-        bnodes = sum(b.nodes for b in probs)
-        with eik.Solver(precision=args.precision, device=local) as sb:
-            outs, st = sb.solve_batch_device(bt, tol=args.tol)
-            ts = []
-            for _ in range(3):
-                flush.fill_(1.0)
-                outs, st = sb.solve_batch_device(bt, tol=args.tol, outs=outs)
-                ts.append(st["seconds"])
-        batch_err = None
-        if cpu is not None:
-            import oracle
-            errs = []
-            for k in (0, 100, 255):
-                r = oracle.fmm(probs[k].F, probs[k].mask, probs[k].q, probs[k].h)
-                errs.append(float(np.max(np.abs(outs[k].cpu().numpy() - r)) / np.max(r)))
-            batch_err = max(errs)
-        extras["batch256"] = {
-            "nodes": bnodes, "nodes_per_s": bnodes / statistics.mean(ts),
-            "ms": statistics.mean(ts) * 1e3, "cell_n": st["cell_n_used"],
-            "max_rel_err_vs_oracle_sampled_3": batch_err}
+        extras["serving"] = run_serving(eik, W, local, args.serve_requests,
+                                        args.serve_unique, tol=args.tol,
+                                        check=cpu is not None)
 
     out = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,

@@ -81,7 +81,7 @@ typedef struct {
                                in microseconds (default 5,000,000); 0 makes
                                every idle wait fail at once (test hook) */
   double bucket_width;      /* width of one queue bucket in units of
-                               (cell edge x mean slowness); <= 0 = default 0.5 */
+                               (cell edge x mean slowness); <= 0 = default 0.25 */
   int max_sweeps_per_visit; /* sweep limit of one cell visit (default 4096) */
   int queue_order;          /* 0 = strict: the next bucket starts once every
                                cell of the current one is finished;
@@ -94,6 +94,10 @@ typedef struct {
                                FP64 polish starts above the fixed point, so
                                this trades bulk sweeps for polish sweeps and
                                does not change the result. */
+  int use_graphs;           /* eik_solve_batch_device: capture the launch
+                               sequence as a CUDA graph and replay it while
+                               the arguments repeat (default 1) */
+  int reserved3;            /* must be 0 */
 } eik_opts;
 
 /* Counters and results of one solve (of the whole batch for batch calls). */
@@ -125,6 +129,9 @@ typedef struct {
   double phase_seconds[2][4];   /* [bulk, polish] x [waiting in the queue pop,
                                    TMA staging, sweeps, write-back + flags + retire],
                                    summed over workers */
+  uint64_t revisits[2];         /* [bulk, polish]: visits of a cell that had
+                                   converged before (restarted at its flagged faces) */
+  uint64_t max_visit_sweeps[3]; /* [bulk, polish, fallback]: most sweeps in one visit */
 } eik_stats;
 
 /* Default options. */
@@ -139,6 +146,11 @@ int eik_destroy(eik_ctx *ctx);
 
 /* Static English text for a status code. */
 const char *eik_strerror(int status);
+
+/* sizeof(eik_opts) and sizeof(eik_stats) as compiled into the library, so
+ * that a binding can check its own copies of the two structs.  Either
+ * pointer may be NULL.  Always returns EIK_OK; needs no device. */
+int eik_struct_sizes(size_t *opts_bytes, size_t *stats_bytes);
 
 /*
  * Solve one grid (Eq. 2), host buffers.
@@ -172,6 +184,20 @@ int eik_solve_device(eik_ctx *ctx, const int64_t dims[3], double h,
                      void *stream, eik_stats *stats);
 
 /*
+ * Autotuner.  Times the solve of a representative grid (host buffers, as
+ * eik_solve) for each cell size in {4, 8, 16} (4 only up to 2^22 nodes) and
+ * one or two cell-kernel CTAs per SM, keeps the fastest for this context,
+ * and uses it for later solves whose size falls in the same power-of-two
+ * bucket of node count while opts.cell_n and opts.max_ctas are 0.  Returns
+ * the choice in *best_n / *best_ctas (either may be NULL).  Cell size 32 is
+ * not offered: a 32^3 cell with its halo does not fit shared memory next to
+ * its slowness.
+ */
+int eik_autotune(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
+                 const uint8_t *src_mask, const double *q, double tol, int *best_n,
+                 int *best_ctas);
+
+/*
  * Solve `count` independent grids in one persistent launch (host buffers).
  * Instance t uses dims[3t..3t+2], h[t], F[t], src_mask[t], q[t], u_out[t].
  * Cells of all instances share one device queue.  stats (may be NULL) sums
@@ -183,7 +209,11 @@ int eik_solve_batch(eik_ctx *ctx, int count, const int64_t *dims,
                     double tol, double *const *u_out, eik_stats *stats);
 
 /* Device-buffer variant of eik_solve_batch (all arrays in device memory;
- * the pointer tables themselves are host arrays). */
+ * the pointer tables themselves are host arrays).  With opts.use_graphs the
+ * first call with a given set of arguments runs plainly and then captures
+ * the whole launch sequence (copies of the small tables, init kernels, the
+ * persistent cell kernels, residual, read-back) as one CUDA graph; later
+ * calls with the same grids, buffers, tolerance and stream replay it. */
 int eik_solve_batch_device(eik_ctx *ctx, int count, const int64_t *dims,
                            const double *h, const float *const *F_dev,
                            const uint8_t *const *src_mask_dev,
@@ -192,14 +222,20 @@ int eik_solve_batch_device(eik_ctx *ctx, int count, const int64_t *dims,
                            eik_stats *stats);
 
 /*
- * Serving.  eik_submit queues one solve (host buffers, same arguments as
- * eik_solve) and returns a ticket at once; the library copies the inputs
- * before returning.  Requests are admitted to the device in arrival order
- * while their memory fits the context budget, run together with the
- * requests already on the device, and write u_out when done.  eik_poll
- * advances the device work and sets *done = 1 once the ticket's u_out is
- * written (its status is then returned).  eik_cancel drops a ticket that
- * has not completed.
+ * Serving (continuous batching).  eik_submit queues one solve (host buffers,
+ * same arguments as eik_solve) and returns a ticket at once.  The library
+ * reads F, src_mask and q, and writes u_out, asynchronously: the caller keeps
+ * all four buffers alive and unchanged until eik_poll reports the ticket
+ * done or eik_cancel succeeds.  Requests are admitted to the device in
+ * arrival order, in batches, on a few concurrent execution slots, while the
+ * memory of the batches on the device fits opts.hbm_budget_bytes; requests
+ * that arrive while others run start as soon as a slot and memory free up.
+ * A request that alone exceeds the budget completes with EIK_EBUDGET.
+ * eik_poll advances the queue (retires finished batches, admits waiting
+ * requests) and sets *done = 1 once the ticket's u_out is written; it then
+ * returns the ticket's status, and the ticket is forgotten.  eik_cancel
+ * drops a ticket that has not completed; a batch already on the device
+ * finishes into a private buffer.  Unknown tickets give EIK_ENOTFOUND.
  */
 int eik_submit(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
                const uint8_t *src_mask, const double *q, double tol,

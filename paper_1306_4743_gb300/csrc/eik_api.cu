@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -50,13 +51,16 @@ struct eik_ctx {
   EncodeTiledFn encode = nullptr;
   // execution slot of the synchronous calls
   Exec main;
+  // execution slot of the captured device-batch graph (its staging is only
+  // written while capturing, so a replay uploads the captured tables)
+  Exec gexec;
   // plane tables, per cell size (index 0: n=4, 1: n=8, 2: n=16)
   unsigned short* d_tab[3] = {nullptr, nullptr, nullptr};
   int* d_off[3] = {nullptr, nullptr, nullptr};
   // serving
   ServeState* serve = nullptr;
-  // autotune cache: log2(nodes) bucket -> cell size
-  std::map<int, int> tuned;
+  // autotune results: log2(nodes) bucket -> (cell size, CTAs of the cell kernel)
+  std::map<int, std::pair<int, int>> tuned;
 };
 
 namespace {
@@ -106,6 +110,7 @@ struct LaunchPlan {
   std::vector<InstPlan> inst;
   int total_cells = 0, max_cells = 0;
   long long max_padded_b = 0, max_padded64 = 0, max_cellnodes = 0, max_nodes = 0;
+  long long max_rows = 0;  // largest ny * nz
   size_t off_key, off_state, off_dir, off_inst, off_next, off_deps, off_down, off_heads, off_ctl,
       off_nsrc;
   size_t off_inst_b, off_inst64, off_tmap_b, off_tmap64, off_prep, off_pol, off_fin;
@@ -119,12 +124,16 @@ size_t take(size_t& cursor, size_t bytes) {
   return at;
 }
 
-int choose_cell_n(eik_ctx* ctx, long long nodes) {
-  if (ctx->opts.cell_n) return ctx->opts.cell_n;
+int size_bucket(long long nodes) {
   int lg = 0;
   while ((1ll << (lg + 1)) <= nodes) ++lg;
-  auto it = ctx->tuned.find(lg);
-  if (it != ctx->tuned.end()) return it->second;
+  return lg;
+}
+
+int choose_cell_n(eik_ctx* ctx, long long nodes) {
+  if (ctx->opts.cell_n) return ctx->opts.cell_n;
+  auto it = ctx->tuned.find(size_bucket(nodes));
+  if (it != ctx->tuned.end()) return it->second.first;
   // built-in size table: 16^3 cells from ~128^3 nodes up (fewer, longer
   // visits keep the queue latency small against the sweeping), else 8^3
   return nodes >= (1ll << 21) ? 16 : 8;
@@ -179,6 +188,7 @@ void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, i
     L.max_padded64 = std::max(L.max_padded64, I.px64 * I.py * I.pz);
     L.max_cellnodes = std::max(L.max_cellnodes, cn);
     L.max_nodes = std::max(L.max_nodes, I.nodes);
+    L.max_rows = std::max(L.max_rows, (long long)I.ny * I.nz);
   }
   L.total_cells = cells;
   L.off_key = take(cur, (size_t)cells * 4);
@@ -212,6 +222,11 @@ int ensure_arena(Exec& ex, size_t bytes, size_t limit) {
     cudaFree(ex.arena);
     ex.arena = nullptr;
     ex.arena_size = 0;
+    if (ex.graph) {  // it points into the old arena
+      cudaGraphExecDestroy(ex.graph);
+      ex.graph = nullptr;
+      ex.graph_key.clear();
+    }
   }
   size_t want = align_up(bytes + bytes / 8, 1 << 20);
   if (limit && want > limit) want = bytes;
@@ -302,6 +317,8 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   int rc = ensure_arena(ex, L.total, arena_limit);
   if (rc) return rc;
   rc = ensure_pinned(&ex.h_small, &ex.h_small_size, L.small_end - L.small_begin);
+  if (rc) return rc;
+  rc = ensure_pinned(&ex.h_ctl, &ex.h_ctl_size, sizeof(Control));
   if (rc) return rc;
   Lr = Launch();
   Lr.count = count;
@@ -449,7 +466,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   Control* dctl = reinterpret_cast<Control*>(A + L.off_ctl);
 
   CK(cudaEventRecord(ex.ev[0], st));
-  double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 0.5;
+  double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 0.25;
   CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), count,
                       L.max_padded_b, L.max_cellnodes, L.max_nodes, L.max_cells, L.total_cells,
                       cells, dctl, reinterpret_cast<int*>(A + L.off_nsrc), !polish, n, wf,
@@ -466,6 +483,10 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.max_sweeps = ctx->opts.max_sweeps_per_visit;
   p.pass = 0;
   p.max_ctas = ctx->opts.max_ctas;
+  if (!p.max_ctas && !ctx->opts.cell_n) {
+    auto it = ctx->tuned.find(size_bucket(nodes_max));
+    if (it != ctx->tuned.end()) p.max_ctas = it->second.second;
+  }
   p.kappa_from_ctl = polish ? 1 : 0;
   p.relaxed = ctx->opts.queue_order;
   p.gated = 0;
@@ -490,16 +511,16 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     // (lift too small), polish again with replace-mode sweeps
     CK(launch_fallback_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol),
                             reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
-                            L.max_nodes, L.max_cells, L.total_cells, cells, dctl, tol, ctx->sms,
+                            L.max_rows, L.max_cells, L.total_cells, cells, dctl, tol, ctx->sms,
                             st));
     p.pass = 2;
     p.gated = 0;
     CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
   }
   CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
-                             L.max_nodes, dctl, ctx->sms, st));
+                             L.max_rows, dctl, polish, tol, ctx->sms, st));
   CK(cudaEventRecord(ex.ev[5], st));
-  Control* hres = hctl;  // reuse the pinned staging for the read-back
+  Control* hres = reinterpret_cast<Control*>(ex.h_ctl);
   CK(cudaMemcpyAsync(hres, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   if (host_io) {
     for (int t = 0; t < count; ++t) {
@@ -559,7 +580,9 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
       stats->phase_seconds[ps][1] = hres->counters[ps][kCntStageNs] * 1e-9;
       stats->phase_seconds[ps][2] = hres->counters[ps][kCntSweepNs] * 1e-9;
       stats->phase_seconds[ps][3] = hres->counters[ps][kCntFlagNs] * 1e-9;
+      stats->revisits[ps] = hres->counters[ps][kCntRevisits];
     }
+    for (int ps = 0; ps < 3; ++ps) stats->max_visit_sweeps[ps] = hres->counters[ps][kCntMaxSweeps];
     stats->precision_used = polish ? EIK_FP32_POLISH : EIK_FP64;
     double r;
     unsigned long long rb = hres->resid_bits;
@@ -628,9 +651,12 @@ int exec_init(Exec& e, bool own_stream) {
 }
 void exec_free(Exec& e) {
   if (e.stream) cudaStreamSynchronize(e.stream);
+  if (e.graph) cudaGraphExecDestroy(e.graph);
+  delete e.graph_launch;
   if (e.arena) cudaFree(e.arena);
   if (e.h_small) cudaFreeHost(e.h_small);
   if (e.h_out) cudaFreeHost(e.h_out);
+  if (e.h_ctl) cudaFreeHost(e.h_ctl);
   for (int i = 0; i < 6; ++i)
     if (e.ev[i]) cudaEventDestroy(e.ev[i]);
   if (e.own_stream && e.stream) cudaStreamDestroy(e.stream);
@@ -651,10 +677,17 @@ int eik_opts_default(eik_opts* o) {
   o->cell_n = 0;
   o->hbm_budget_bytes = 0;
   o->spin_cap_us = 5000000ull;
-  o->bucket_width = 0.5;
+  o->bucket_width = 0.25;
   o->max_sweeps_per_visit = 4096;
   o->bulk_kappa_rel = 3.0e-5;
   o->queue_order = 1;
+  o->use_graphs = 1;
+  return EIK_OK;
+}
+
+int eik_struct_sizes(size_t* opts_bytes, size_t* stats_bytes) {
+  if (opts_bytes) *opts_bytes = sizeof(eik_opts);
+  if (stats_bytes) *stats_bytes = sizeof(eik_stats);
   return EIK_OK;
 }
 
@@ -685,10 +718,10 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
   }
   if (o.precision != EIK_FP64 && o.precision != EIK_FP32_POLISH) return EIK_EINVAL;
   if (o.cell_n != 0 && size_index(o.cell_n) < 0) return EIK_EINVAL;
-  if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1) return EIK_EINVAL;
+  if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1 || o.reserved3) return EIK_EINVAL;
   if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
   if (!(o.bulk_kappa_rel >= 0.0) || isinf(o.bulk_kappa_rel)) return EIK_EINVAL;
-  if (!(o.bucket_width > 0.0)) o.bucket_width = 0.5;
+  if (!(o.bucket_width > 0.0)) o.bucket_width = 0.25;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
     cudaGetLastError();
@@ -730,6 +763,7 @@ int eik_destroy(eik_ctx* c) {
   if (c->serve) serve_destroy(c->serve);
   if (c->stream) cudaStreamSynchronize(c->stream);
   exec_free(c->main);
+  exec_free(c->gexec);
   for (int i = 0; i < 3; ++i) {
     if (c->d_tab[i]) cudaFree(c->d_tab[i]);
     if (c->d_off[i]) cudaFree(c->d_off[i]);
@@ -756,6 +790,45 @@ int eik_solve_device(eik_ctx* ctx, const int64_t dims[3], double h, const float*
                        reinterpret_cast<cudaStream_t>(stream), stats, 0);
 }
 
+int eik_autotune(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
+                 const uint8_t* src_mask, const double* q, double tol, int* best_n,
+                 int* best_ctas) {
+  if (!ctx || !dims || !F || !src_mask || !q) return EIK_EINVAL;
+  const long long nodes = (long long)dims[0] * dims[1] * dims[2];
+  double* u = static_cast<double*>(malloc((size_t)nodes * sizeof(double)));
+  if (!u) return EIK_ENOMEM;
+  const eik_opts saved = ctx->opts;
+  const int cands_n[3] = {4, 8, 16};
+  double best = 1e300;
+  int bn = 0, bc = 0, rc = EIK_OK;
+  for (int ci = 0; ci < 3 && rc == EIK_OK; ++ci) {
+    const int n = cands_n[ci];
+    if (n == 4 && nodes > (1ll << 22)) continue;  // many small cells: queue-bound
+    for (int per_sm = 1; per_sm <= 2; ++per_sm) {
+      ctx->opts.cell_n = n;
+      ctx->opts.max_ctas = per_sm * ctx->sms;
+      double t = 0.0;
+      for (int rep = 0; rep < 2 && rc == EIK_OK; ++rep) {  // first run warms up
+        eik_stats st;
+        rc = eik_solve(ctx, dims, h, F, src_mask, q, tol, u, &st);
+        t = st.seconds;
+      }
+      if (rc == EIK_OK && t < best) {
+        best = t;
+        bn = n;
+        bc = per_sm * ctx->sms;
+      }
+    }
+  }
+  ctx->opts = saved;
+  free(u);
+  if (rc != EIK_OK) return rc;
+  ctx->tuned[size_bucket(nodes)] = std::make_pair(bn, bc);
+  if (best_n) *best_n = bn;
+  if (best_ctas) *best_ctas = bc;
+  return EIK_OK;
+}
+
 int eik_solve_batch(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
                     const float* const* F, const uint8_t* const* src_mask,
                     const double* const* q, double tol, double* const* u_out, eik_stats* stats) {
@@ -769,8 +842,85 @@ int eik_solve_batch_device(eik_ctx* ctx, int count, const int64_t* dims, const d
                            const double* const* q_dev, double tol, double* const* u_out_dev,
                            void* stream, eik_stats* stats) {
   if (!ctx) return EIK_EINVAL;
-  return eik_run_batch(ctx, count, dims, h, F_dev, src_mask_dev, q_dev, tol, u_out_dev, false,
-                       reinterpret_cast<cudaStream_t>(stream), stats, 0);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!ctx->opts.use_graphs || count < 1 || !dims || !h || !F_dev || !src_mask_dev || !q_dev ||
+      !u_out_dev)
+    return eik_run_batch(ctx, count, dims, h, F_dev, src_mask_dev, q_dev, tol, u_out_dev, false,
+                         st, stats, 0);
+  // The whole launch sequence of this batch is captured once as a CUDA graph
+  // and replayed while every argument is the same (same grids, buffers and
+  // options: the arena layout and the tensor maps then match too).
+  Exec& ex = ctx->gexec;
+  if (!ex.ev[0] && exec_init(ex, false) != EIK_OK) return EIK_ECUDA;
+  std::vector<unsigned long long> key;
+  key.push_back((unsigned long long)count);
+  unsigned long long tb;
+  memcpy(&tb, &tol, 8);
+  key.push_back(tb);
+  key.push_back((unsigned long long)(uintptr_t)st);
+  for (int t = 0; t < count; ++t) {
+    for (int a = 0; a < 3; ++a) key.push_back((unsigned long long)dims[3 * t + a]);
+    unsigned long long hb;
+    memcpy(&hb, &h[t], 8);
+    key.push_back(hb);
+    key.push_back((unsigned long long)(uintptr_t)F_dev[t]);
+    key.push_back((unsigned long long)(uintptr_t)src_mask_dev[t]);
+    key.push_back((unsigned long long)(uintptr_t)q_dev[t]);
+    key.push_back((unsigned long long)(uintptr_t)u_out_dev[t]);
+  }
+  if (!(ex.graph && key == ex.graph_key && ex.graph_launch)) {
+    // first call with these arguments: run it plainly (this also sizes the
+    // arena and staging), then capture the same sequence for later calls
+    Launch plain;
+    int rc = eik_launch_batch(ctx, ex, count, dims, h, F_dev, src_mask_dev, q_dev, tol, u_out_dev,
+                              false, st, false, plain, ctx->opts.hbm_budget_bytes, 0);
+    if (rc != EIK_OK) {
+      cudaStreamSynchronize(st);
+      cudaGetLastError();
+      return rc;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return EIK_ECUDA;
+    }
+    rc = eik_finish_batch(ctx, ex, plain, stats);
+    if (rc != EIK_OK) return rc;
+    if (ex.graph) {
+      cudaGraphExecDestroy(ex.graph);
+      ex.graph = nullptr;
+    }
+    ex.graph_key.clear();
+    if (!ex.graph_launch) ex.graph_launch = new (std::nothrow) Launch();
+    if (!ex.graph_launch) return EIK_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return EIK_OK;  // graphs unavailable on this stream: stay with plain launches
+    }
+    const int lrc = eik_launch_batch(ctx, ex, count, dims, h, F_dev, src_mask_dev, q_dev, tol,
+                                     u_out_dev, false, st, false, *ex.graph_launch,
+                                     ctx->opts.hbm_budget_bytes, 0);
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (lrc != EIK_OK || ce != cudaSuccess || !g) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return EIK_OK;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&ex.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      ex.graph = nullptr;
+      return EIK_OK;
+    }
+    ex.graph_key = key;
+    return EIK_OK;
+  }
+  if (cudaGraphLaunch(ex.graph, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return EIK_ECUDA;
+  }
+  return eik_finish_batch(ctx, ex, *ex.graph_launch, stats);
 }
 
 }  // extern "C"

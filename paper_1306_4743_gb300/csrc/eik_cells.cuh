@@ -56,10 +56,13 @@ struct Geo {
   static constexpr int UBYTES = BX * BY * BZ * ES;
   static constexpr int SBYTES = N3 * ES;
   static constexpr int align128(int b) { return (b + 127) / 128 * 128; }
-  // per-worker shared memory: u tile | s tile | change flags | mbarrier + scratch
+  // per-worker shared memory: u tile | s tile | change flags | plane list |
+  // mbarrier + scratch
   static constexpr int OFF_S = align128(UBYTES);
   static constexpr int OFF_CHG = OFF_S + align128(SBYTES);
-  static constexpr int OFF_BAR = OFF_CHG + align128(N3);
+  // active-node list of one plane (at most N^2 nodes lie on a plane)
+  static constexpr int OFF_LIST = OFF_CHG + align128(N3);
+  static constexpr int OFF_BAR = OFF_LIST + align128(N * N * 2);
   static constexpr int WORKER_BYTES = OFF_BAR + 128;
   // CTA-wide: plane table | plane offsets
   static constexpr int TAB_BYTES = align128(N3 * 2);
@@ -84,82 +87,232 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
   }
 }
 
-// One directional sweep of a staged cell.  Returns (worker-wide) whether a
-// node changed by more than the threshold.
-template <typename T, int N, int WPC, bool REPLACE>
-__device__ __forceinline__ bool sweep_cell(T* __restrict__ U, const T* __restrict__ S,
-                                           unsigned char* __restrict__ chg,
-                                           const unsigned short* __restrict__ tab,
-                                           const int* __restrict__ off, int dir, int tid,
-                                           int worker, T kappa, unsigned& n_updates) {
+// Alg. 2 for one node (i, j, k) of the staged cell that is active: clear
+// its active bit, recompute it from its six neighbours (Eq. 2), store a
+// lower value (min mode) or any new value (replace mode), and on a change
+// by more than the threshold activate the neighbours that may now use it.
+// `left` records, per axis (bit 0 x, 1 y, 2 z), an activation on the plane
+// the sweep has just left.
+template <typename T, int N, bool REPLACE>
+__device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
+                                            unsigned char* __restrict__ chg, int i, int j, int k,
+                                            int fx, int fy, int fz, T kappa,
+                                            unsigned& n_updates, unsigned& left) {
   using G = Geo<T, N>;
-  constexpr int NT = WPC * 32;
+  const int si = i + N * (j + N * k);
+  const T s = S[si];
+  unsigned char c1 = chg[si] & (unsigned char)~kActive;  // Alg. 2 l.4
+  if (s < tinf<T>()) {
+    const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+    const T v = U[t];
+    const T xm = U[t - 1], xp = U[t + 1];
+    const T ym = U[t - G::SY], yp = U[t + G::SY];
+    const T zm = U[t - G::SZ], zp = U[t + G::SZ];
+    const T vk = v - kappa;  // off the solve's dependency chain
+    const T nv = local_solve(nmin(xm, xp), nmin(ym, yp), nmin(zm, zp), s);
+    ++n_updates;
+    bool big;
+    if constexpr (!REPLACE) {
+      const bool lower = vlt(nv, v);
+      big = vlt(nv, vk);
+      if (lower) {
+        U[t] = nv;
+        c1 |= big ? 3 : 1;
+      }
+    } else {
+      big = nv != v && fabs(nv - v) > kappa + fabs(v) * (T)8.8817841970012523e-16;
+      if (nv != v) {
+        U[t] = nv;
+        c1 |= big ? 3 : 1;
+      }
+    }
+    if (big) {
+      // Alg. 2 l.8-10: neighbours (in this cell) that may now use the new
+      // value become active; neighbours in other cells are reached through
+      // the face flags.  The neighbour on the side the sweep came from lies
+      // on the previous plane.
+      if (i > 0 && (REPLACE || xm > nv)) {
+        chg[si - 1] |= kActive;
+        left |= fx == 0 ? 1u : 0u;
+      }
+      if (i < N - 1 && (REPLACE || xp > nv)) {
+        chg[si + 1] |= kActive;
+        left |= fx != 0 ? 1u : 0u;
+      }
+      if (j > 0 && (REPLACE || ym > nv)) {
+        chg[si - N] |= kActive;
+        left |= fy == 0 ? 2u : 0u;
+      }
+      if (j < N - 1 && (REPLACE || yp > nv)) {
+        chg[si + N] |= kActive;
+        left |= fy != 0 ? 2u : 0u;
+      }
+      if (k > 0 && (REPLACE || zm > nv)) {
+        chg[si - N * N] |= kActive;
+        left |= fz == 0 ? 4u : 0u;
+      }
+      if (k < N - 1 && (REPLACE || zp > nv)) {
+        chg[si + N * N] |= kActive;
+        left |= fz != 0 ? 4u : 0u;
+      }
+    }
+  }
+  chg[si] = c1;
+}
+
+// Worker-wide OR of the three axis bits.
+template <int WPC>
+__device__ __forceinline__ unsigned worker_or3(int worker, unsigned bits) {
+  if constexpr (WPC == 1) {
+    return __reduce_or_sync(0xffffffffu, bits);
+  } else {
+    unsigned r = 0;
+    if (bar_red_or(1 + worker, WPC * 32, (bits & 1u) != 0)) r |= 1u;
+    if (bar_red_or(1 + worker, WPC * 32, (bits & 2u) != 0)) r |= 2u;
+    if (bar_red_or(1 + worker, WPC * 32, (bits & 4u) != 0)) r |= 4u;
+    return r;
+  }
+}
+
+// First and last plane (in the order of direction `dir`) that hold an
+// active node; first > last when no node is active.  `ws` is 2 * WPC ints
+// of worker scratch.
+template <int N, int WPC>
+__device__ __forceinline__ void active_planes(const unsigned char* __restrict__ chg, int dir,
+                                              int tid, int worker, int* ws, int& first,
+                                              int& last) {
+  constexpr int NT = WPC * 32, N3 = N * N * N;
   const int fx = (dir & 1) ? N - 1 : 0;
   const int fy = (dir & 2) ? N - 1 : 0;
   const int fz = (dir & 4) ? N - 1 : 0;
-  bool changed = false;
-  for (int C = 0; C < G::NPLANES; ++C) {
+  int lo = 1 << 20, hi = -1;
+  for (int e = tid * 16; e < N3; e += NT * 16) {
+    const uint4 w = *reinterpret_cast<const uint4*>(chg + e);
+    const unsigned wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unsigned act = wd[q] & 0x04040404u;
+      while (act) {
+        const int b = (__ffs(act) - 1) >> 3;
+        act &= act - 1u;
+        const int idx = e + 4 * q + b;
+        const int pl = ((idx % N) ^ fx) + (((idx / N) % N) ^ fy) + ((idx / (N * N)) ^ fz);
+        lo = pl < lo ? pl : lo;
+        hi = pl > hi ? pl : hi;
+      }
+    }
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if constexpr (WPC > 1) {
+    const int wwarp = tid >> 5;
+    if ((tid & 31) == 0) {
+      ws[wwarp] = lo;
+      ws[WPC + wwarp] = hi;
+    }
+    worker_sync<WPC>(worker);
+#pragma unroll
+    for (int w2 = 0; w2 < WPC; ++w2) {
+      lo = ws[w2] < lo ? ws[w2] : lo;
+      hi = ws[WPC + w2] > hi ? ws[WPC + w2] : hi;
+    }
+  }
+  first = lo;
+  last = hi;
+}
+
+// One directional sweep of a staged cell over planes first.. of the order
+// of `dir`, where `last` is the last plane holding a node that was active
+// when the sweep began.  A node's six neighbours lie on the planes just
+// before and just after its own, so a node activated on the next plane is
+// swept later in this same sweep; past `last`, a plane with no active node
+// ends the sweep, as no later plane can hold one.  Returns (worker-wide)
+// the axes along which a node on the plane just left was activated: the
+// nodes still active afterwards.  With none, another sweep would change
+// nothing, so the cell has converged one sweep earlier than the plain
+// "until a sweep changes nothing" test would find.
+//
+// COMPACT (one-warp workers): the active nodes of each plane are first
+// gathered into a list by ballot and the lanes then take list entries, so
+// the warp issues a node's arithmetic only for nodes that need it.  This
+// matters for FP64, whose narrow pipe costs the same per warp instruction
+// however few lanes are active.
+template <typename T, int N, int WPC, bool REPLACE, bool COMPACT>
+__device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __restrict__ S,
+                                               unsigned char* __restrict__ chg,
+                                               const unsigned short* __restrict__ tab,
+                                               const int* __restrict__ off,
+                                               unsigned short* __restrict__ list, int dir,
+                                               int first, int last, int tid, int worker,
+                                               T kappa, unsigned& n_updates) {
+  using G = Geo<T, N>;
+  constexpr int NT = WPC * 32;
+  static_assert(!COMPACT || WPC == 1, "the gathered list is per warp");
+  const int fx = (dir & 1) ? N - 1 : 0;
+  const int fy = (dir & 2) ? N - 1 : 0;
+  const int fz = (dir & 4) ? N - 1 : 0;
+  unsigned left = 0;
+  for (int C = first; C < G::NPLANES; ++C) {
     const int beg = off[C], end = off[C + 1];
     // Nodes of one plane do not depend on each other: each thread takes UNR
     // per pass, so their loads and arithmetic overlap.
     constexpr int UNR = (N >= 16 && WPC == 1) ? 3 : 2;
-    for (int e0 = beg + tid; e0 < end; e0 += UNR * NT) {
+    bool any;
+    if constexpr (!COMPACT) {
+      bool did = false;
+      for (int e0 = beg + tid; e0 < end; e0 += UNR * NT) {
 #pragma unroll
-      for (int h = 0; h < UNR; ++h) {
-        const int e = e0 + h * NT;
-        if (e >= end) break;
-        const unsigned pk = tab[e];
-        const int i = (int)(pk & 31u) ^ fx;
-        const int j = (int)((pk >> 5) & 31u) ^ fy;
-        const int k = (int)((pk >> 10) & 31u) ^ fz;
-        const int si = i + N * (j + N * k);
-        const unsigned char c0 = chg[si];
-        if (!(c0 & kActive)) continue;  // Alg. 2 l.1-2: inactive, nothing to do
-        const T s = S[si];
-        unsigned char c1 = c0 & (unsigned char)~kActive;  // Alg. 2 l.4
-        if (s < tinf<T>()) {
-          const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
-          const T v = U[t];
-          const T xm = U[t - 1], xp = U[t + 1];
-          const T ym = U[t - G::SY], yp = U[t + G::SY];
-          const T zm = U[t - G::SZ], zp = U[t + G::SZ];
-          const T vk = v - kappa;  // off the solve's dependency chain
-          const T nv = local_solve(nmin(xm, xp), nmin(ym, yp), nmin(zm, zp), s);
-          ++n_updates;
-          bool big;
-          if constexpr (!REPLACE) {
-            const bool lower = vlt(nv, v);
-            big = vlt(nv, vk);
-            if (lower) {
-              U[t] = nv;
-              c1 |= big ? 3 : 1;
-            }
-          } else {
-            big = nv != v && fabs(nv - v) > kappa + fabs(v) * (T)8.8817841970012523e-16;
-            if (nv != v) {
-              U[t] = nv;
-              c1 |= big ? 3 : 1;
-            }
-          }
-          if (big) {
-            changed = true;
-            // Alg. 2 l.8-10: neighbours (in this cell) that may now use the
-            // new value become active; neighbours in other cells are reached
-            // through the face flags.
-            if (i > 0 && (REPLACE || xm > nv)) chg[si - 1] |= kActive;
-            if (i < N - 1 && (REPLACE || xp > nv)) chg[si + 1] |= kActive;
-            if (j > 0 && (REPLACE || ym > nv)) chg[si - N] |= kActive;
-            if (j < N - 1 && (REPLACE || yp > nv)) chg[si + N] |= kActive;
-            if (k > 0 && (REPLACE || zm > nv)) chg[si - N * N] |= kActive;
-            if (k < N - 1 && (REPLACE || zp > nv)) chg[si + N * N] |= kActive;
-          }
+        for (int h = 0; h < UNR; ++h) {
+          const int e = e0 + h * NT;
+          if (e >= end) break;
+          const unsigned pk = tab[e];
+          const int i = (int)(pk & 31u) ^ fx;
+          const int j = (int)((pk >> 5) & 31u) ^ fy;
+          const int k = (int)((pk >> 10) & 31u) ^ fz;
+          if (!(chg[i + N * (j + N * k)] & kActive)) continue;  // Alg. 2 l.1-2
+          did = true;
+          update_node<T, N, REPLACE>(U, S, chg, i, j, k, fx, fy, fz, kappa, n_updates, left);
         }
-        chg[si] = c1;
       }
+      any = worker_any<WPC>(worker, did);  // also ends the plane
+    } else {
+      // gather the plane's active nodes (as direction-applied i | j << 5 | k << 10)
+      const int lane = tid & 31;
+      const unsigned below = (1u << lane) - 1u;
+      int total = 0;
+      for (int e0 = beg; e0 < end; e0 += 32) {
+        const int e = e0 + lane;
+        bool act = false;
+        unsigned pk = 0;
+        if (e < end) {
+          const unsigned q = tab[e];
+          const int i = (int)(q & 31u) ^ fx, j = (int)((q >> 5) & 31u) ^ fy,
+                    k = (int)((q >> 10) & 31u) ^ fz;
+          act = (chg[i + N * (j + N * k)] & kActive) != 0;
+          pk = (unsigned)i | ((unsigned)j << 5) | ((unsigned)k << 10);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (act) list[total + __popc(m & below)] = (unsigned short)pk;
+        total += __popc(m);
+      }
+      __syncwarp();
+      for (int x0 = tid; x0 < total; x0 += UNR * NT) {
+#pragma unroll
+        for (int h = 0; h < UNR; ++h) {
+          const int x = x0 + h * NT;
+          if (x >= total) break;
+          const unsigned pk = list[x];
+          update_node<T, N, REPLACE>(U, S, chg, (int)(pk & 31u), (int)((pk >> 5) & 31u),
+                                     (int)((pk >> 10) & 31u), fx, fy, fz, kappa, n_updates,
+                                     left);
+        }
+      }
+      any = total > 0;
+      worker_sync<WPC>(worker);
     }
-    worker_sync<WPC>(worker);
+    if (!any && C >= last) break;
   }
-  return worker_any<WPC>(worker, changed);
+  return worker_or3<WPC>(worker, left);
 }
 
 template <typename T, int N, int WPC, int WORKERS, bool REPLACE>
@@ -182,7 +335,10 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   T* S = reinterpret_cast<T*>(wbase + G::OFF_S);
   unsigned char* chg = wbase + G::OFF_CHG;
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(wbase + G::OFF_BAR);
-  int* wshared = reinterpret_cast<int*>(wbase + G::OFF_BAR + 16);  // [0]=cell [1]=dirs
+  // scratch: [0] cell, [1] direction word, [2..7] face keys, [12..19] plane range
+  int* wshared = reinterpret_cast<int*>(wbase + G::OFF_BAR + 16);
+  unsigned short* list = reinterpret_cast<unsigned short*>(wbase + G::OFF_LIST);
+  constexpr bool COMPACT = sizeof(T) == 8 && WPC == 1;
 
   if (tid == 0) mbar_init(bar, 1);
   fence_proxy_async_smem();
@@ -192,7 +348,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   const CellArrays& cells = p.cells;
   unsigned phase = 0;
   unsigned slot = 0;  // ring slot of the bucket the current cell came from
-  unsigned long long n_visits = 0, n_sweeps = 0, n_pushes = 0, busy_ns = 0;
+  unsigned long long n_visits = 0, n_sweeps = 0, n_pushes = 0, busy_ns = 0, n_revisits = 0;
   unsigned long long pop_ns = 0, stage_ns = 0, sweep_ns = 0, flag_ns = 0;
   unsigned n_updates = 0;
   unsigned long long upd_total = 0;
@@ -201,14 +357,14 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   for (;;) {
     // ---- 1. pop --------------------------------------------------------
     int cell = -1;
-    unsigned pref = 0;
+    unsigned pref = 0;  // direction word as taken: preferred dirs, faces, visited
     unsigned long long t_pop0 = 0;
     if (tid == 0) t_pop0 = global_timer_ns();
     if (wwarp == 0) {
       cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane, &slot, p.relaxed != 0);
       if (lane == 0 && cell >= 0) {
         atomicExch(cells.key + cell, kKeyInf);        // V^c <- +inf (Alg. 1 l.5)
-        pref = atomicExch(cells.dir + cell, 0u) & 0xffu;  // take preferred dirs
+        pref = atomicAnd(cells.dir + cell, kDirVisited);  // take dirs and faces
       }
       pref = __shfl_sync(0xffffffffu, pref, 0);
       if constexpr (WPC > 1) {
@@ -248,10 +404,16 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       tma_load_3d(U, p.tmaps + ii, N * cx, N * cy, N * cz, bar);
       bulk_load(S, static_cast<const T*>(I.s) + (size_t)lc * G::N3, (unsigned)G::SBYTES, bar);
     }
-    // every node starts active: the halo may have changed since the last visit
-    for (int e = tid * 16; e < G::N3; e += NT * 16)
-      *reinterpret_cast<uint4*>(chg + e) = make_uint4(0x04040404u, 0x04040404u, 0x04040404u,
-                                                      0x04040404u);
+    // On a first visit every node starts active.  After a converged visit
+    // only the halo can have changed (a cell's nodes have one writer, the
+    // cell), so only the nodes on the faces flagged since then start active.
+    const bool revisit = (pref & kDirVisited) != 0;
+    const unsigned faces = (pref >> kFaceShift) & 0x3fu;
+    {
+      const unsigned fill = revisit ? 0u : 0x04040404u;
+      for (int e = tid * 16; e < G::N3; e += NT * 16)
+        *reinterpret_cast<uint4*>(chg + e) = make_uint4(fill, fill, fill, fill);
+    }
     {
       unsigned long long spins = 0;
       while (!mbar_try_wait(bar, phase)) {
@@ -266,6 +428,20 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     }
     phase ^= 1u;
     worker_sync<WPC>(worker);
+    if (revisit) {
+      for (int f = 0; f < 6; ++f) {
+        if (!((faces >> f) & 1u)) continue;
+        const int axis = f >> 1, side = (f & 1) ? N - 1 : 0;
+        for (int q = tid; q < N * N; q += NT) {
+          const int a = q % N, b = q / N;
+          const int e = axis == 0 ? side + N * (a + N * b)
+                      : axis == 1 ? a + N * (side + N * b)
+                                  : a + N * (b + N * side);
+          chg[e] = kActive;
+        }
+      }
+      worker_sync<WPC>(worker);
+    }
     unsigned long long t_sw = 0;
     if (tid == 0) {
       t_sw = global_timer_ns();
@@ -273,27 +449,47 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     }
 
     // ---- 3. sweeps -----------------------------------------------------
+    // Min mode: the first preferred direction (in the standard order), then
+    // each next sweep reverses the axes along which the last one left
+    // active nodes behind.  Replace mode: every preferred direction, then
+    // the standard loop.  A sweep
+    // covers only the planes from the first one holding an active node.
     int nsw = 0;
     bool converged = false;
-    // preferred directions first, in the standard order
+    bool all_active = !revisit;  // every node active: no need to look
+    int dlast = -1;
+    unsigned lm = 0;
+    auto run = [&](int d) {
+      int first = 0, last = G::NPLANES - 1;
+      if (!all_active) active_planes<N, WPC>(chg, d, tid, worker, wshared + 12, first, last);
+      all_active = false;
+      dlast = d;
+      if (first > last) {
+        lm = 0;  // nothing active: converged without a sweep
+        return;
+      }
+      lm = sweep_cell<T, N, WPC, REPLACE, COMPACT>(U, S, chg, tab, off, list, d, first, last, tid,
+                                                   worker, kappa, n_updates);
+      ++nsw;
+    };
     for (int r = 0; r < 8 && !converged; ++r) {
       const int d = kStdOrder[r];
-      if (!((pref >> d) & 1u)) continue;
-      const bool ch = sweep_cell<T, N, WPC, REPLACE>(U, S, chg, tab, off, d, tid, worker, kappa,
-                                                     n_updates);
-      ++nsw;
-      if (!ch) converged = true;
+      if (!((pref >> d) & 1u)) continue;  // bits 0-7: preferred directions
+      run(d);
+      if (!lm) converged = true;
+      if (!REPLACE) break;  // min mode: the first one, then the adaptive order
     }
-    // then the standard loop until a sweep changes nothing
     for (int r = 0; !converged; r = (r + 1) & 7) {
       if (nsw >= p.max_sweeps) break;
-      const bool ch = sweep_cell<T, N, WPC, REPLACE>(U, S, chg, tab, off, kStdOrder[r], tid,
-                                                     worker, kappa, n_updates);
-      ++nsw;
-      if (!ch) converged = true;
+      run((!REPLACE && dlast >= 0) ? (dlast ^ (int)lm) : kStdOrder[r]);
+      if (!lm) converged = true;
     }
     upd_total += n_updates;
     n_updates = 0;
+    if (tid == 0) {
+      if (converged) atomicOr(cells.dir + cell, kDirVisited);
+      else atomicAnd(cells.dir + cell, ~kDirVisited);
+    }
     if (!converged) {
       if constexpr (REPLACE) {
         if (tid == 0) atomicOr(cells.state + cell, kStDirty);  // visit again later
@@ -318,20 +514,6 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       const int nlim = axis == 0 ? I.ncx : axis == 1 ? I.ncy : I.ncz;
       unsigned m = 0xffffffffu;
       if (ncoord >= 0 && ncoord < nlim) {  // warp-uniform
-        // Polish: a neighbour cell not yet visited still holds its lifted
-        // start values V0 = U32 (1 + 2^-11); its fixed-point values are at
-        // most U32 (1 + 2^-15) (the FP32 error bound), so the border test
-        // compares with V0 scaled back to that bound instead of V0 itself.
-        T shrink = (T)1;
-        if (!REPLACE && p.gated) {
-          const int nlc = axis == 0 ? lc + (upper ? 1 : -1)
-                        : axis == 1 ? lc + (upper ? I.ncx : -I.ncx)
-                                    : lc + (upper ? I.ncx * I.ncy : -I.ncx * I.ncy);
-          unsigned vis = 0;
-          if (lane == 0) vis = ld_relaxed_u32(cells.down + I.cell_base + nlc) & 0x100u;
-          vis = __shfl_sync(0xffffffffu, vis, 0);
-          if (!vis) shrink = (T)0.99954229454883116;  // (1 + 2^-15) / (1 + 2^-11)
-        }
         for (int q = lane; q < N * N; q += 32) {
           const int a = q % N, b = q / N;
           int i, j, k;
@@ -342,7 +524,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
             const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
             const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
             const T vi = U[t];
-            const T vj = U[upper ? t + step : t - step] * shrink;  // halo value
+            const T vj = U[upper ? t + step : t - step];  // halo value
             // Min mode: only a border value below its neighbour's can be
             // used by the neighbour, and the (possibly stale) halo value is
             // never below the neighbour's current one, so this test misses
@@ -384,6 +566,8 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
         unsigned dirs = 0;
         for (int d = 0; d < 8; ++d)
           if (((d & bit) != 0) == (upper == 0)) dirs |= 1u << d;
+        // the neighbour sees the change on its opposite face
+        dirs |= 1u << (kFaceShift + 2 * axis + (upper ^ 1));
         flag_cell(cells, ctl, nb, m, dirs, &n_pushes, p.gated != 0);
       }
       if (p.gated) {
@@ -413,6 +597,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       retire_cell(cells, ctl, (unsigned)cell, slot, &n_pushes);
       busy_ns += global_timer_ns() - t_pop;
       ++n_visits;
+      if (revisit) ++n_revisits;
       // the watchdog only needs to see that visits complete: publish every 8th
       if ((n_visits & 7u) == 1u) atomicAdd(&ctl->progress, 8u);
       n_sweeps += (unsigned long long)nsw;
@@ -426,6 +611,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   if (tid == 0) {
     if (n_visits) atomicAdd(cnt + kCntVisits, n_visits);
     if (n_sweeps) atomicAdd(cnt + kCntSweeps, n_sweeps);
+    if (n_revisits) atomicAdd(cnt + kCntRevisits, n_revisits);
     if (max_sweeps_seen) atomicMax(cnt + kCntMaxSweeps, (unsigned long long)max_sweeps_seen);
     if (busy_ns) atomicAdd(cnt + kCntBusyNs, busy_ns);
     atomicAdd(cnt + kCntPopNs, pop_ns);

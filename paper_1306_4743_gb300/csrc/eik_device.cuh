@@ -249,15 +249,17 @@ __device__ __forceinline__ bool dlt_nn(double a, double b) { return dbits(a) < d
 // f' only scales the tiny correction, so 1/f' is taken in FP32.  The
 // one-term root is exact (U = a1 + s).  Near a branch boundary the m-term
 // roots of both branches agree to O(e0^2 / s), so the FP32 choice of m
-// costs nothing.  The FP64 part is four dependent operations deep.
+// costs nothing.  The FP64 part is four dependent operations deep on the
+// two- and three-term paths (b_d, then r_d and a1 + w, then f, then U).
 __device__ __forceinline__ double local_solve(double ax, double ay, double az, double s) {
   const double lo = dmin_nn(ax, ay), hi = dmax_nn(ax, ay);
   const double a1 = dmin_nn(lo, az), mid = dmax_nn(lo, az);
   const double a2 = dmin_nn(hi, mid), a3 = dmax_nn(hi, mid);
-  const double u1 = a1 + s;
-  if (dle_nn(u1, a2)) return u1;  // one term, exact; also a1 = +inf
-  const double b2 = a2 - a1, b3 = a3 - a1;
-  const double s2 = s * s;
+  const double b2 = a2 - a1, b3 = a3 - a1, s2 = s * s;
+  // One term when a1 + s <= a2, tested as s <= b2 so that the sum stays off
+  // the two- and three-term paths; a1 = +inf (no information) also returns
+  // a1 + s = +inf.  Both tests run on the integer pipe.
+  if (dle_nn(s, b2) || dbits(a1) >= dbits(CUDART_INF)) return a1 + s;
   const float fs = f32_of_f64_nn(s), fb2 = f32_of_f64_nn(b2), fb3 = f32_of_f64_nn(b3);
   const float fs2 = fs * fs;
   const float w2 = 0.5f * (fb2 + sqrt_fast(fmaxf(2.0f * fs2 - fb2 * fb2, 0.0f)));
@@ -476,7 +478,10 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
     }
     // Nothing to take: wait for running cells, with a no-progress limit.
     int timed_out = 0;
-    if (lane == 0 && (polls & 15u) == 1u) {
+    if (lane == 0 && spin_cap_ns == 0) {  // the test hook: no idle wait at all
+      set_status(ctl, EIK_ETIMEOUT);
+      timed_out = 1;
+    } else if (lane == 0 && (polls & 15u) == 1u) {
       const unsigned prog = ld_acquire_u32(&ctl->progress);
       const unsigned long long now = global_timer_ns();
       if (prog != last_prog) {

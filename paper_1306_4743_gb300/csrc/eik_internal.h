@@ -28,6 +28,15 @@ constexpr unsigned kStQueued = 1u;   // in exactly one bucket stack
 constexpr unsigned kStRunning = 2u;  // being swept by one worker
 constexpr unsigned kStDirty = 4u;    // new inflow data arrived after the last load
 
+// Cell direction word: bits 0-7 preferred sweep directions, bits 8-13 the
+// faces whose halo values changed since the cell was last staged, bit 16
+// set once a visit of the cell has converged (its interior is then a fixed
+// point for the halo it saw, so the next visit need only restart at the
+// flagged faces).
+constexpr unsigned kDirMask = 0xffu;
+constexpr int kFaceShift = 8;
+constexpr unsigned kDirVisited = 1u << 16;
+
 // Counters, in device memory (unsigned long long each).
 enum CounterIndex {
   kCntVisits = 0,
@@ -40,6 +49,7 @@ enum CounterIndex {
   kCntSweepNs,    //               sweeps
   kCntFlagNs,     //               write-back and flags
   kCntPopNs,      // time spent in the pop loop (waiting included)
+  kCntRevisits,   // visits of a cell that had converged before
   kNumCounters
 };
 

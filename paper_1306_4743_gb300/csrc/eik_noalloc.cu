@@ -276,8 +276,8 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.gated = 0;
   int grid = 0;
   CKN(launch_cells(true, false, n, p, slot->sms, st, &grid));
-  CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), 1, nodes, dctl,
-                              slot->sms, st));
+  CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), 1,
+                              (long long)ny * nz, dctl, false, 0.0, slot->sms, st));
   CKN(cudaMemcpyAsync(&g_host_ctl, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   CKN(cudaStreamSynchronize(st));
 

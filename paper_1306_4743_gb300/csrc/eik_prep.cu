@@ -402,6 +402,11 @@ __global__ void setup_polish_kernel(Control* ctl, int gated, double kappa) {
   if (threadIdx.x || blockIdx.x) return;
   if (ctl->status) return;
   if (gated && !fallback_needed(ctl, kappa)) return;
+  if (gated) {  // the final statistics are taken again after the fallback
+    ctl->resid_bits = 0ull;
+    ctl->final_umax_bits = 0ull;
+    ctl->nonfinite = 0ull;
+  }
   const double umax = double_of_ord(ctl->umax_bits);
   double width = 1.0 / (double)ctl->inv_width;
   const double span = umax - (double)ctl->base;
@@ -430,53 +435,63 @@ __global__ void seed_all_kernel(int total_cells, CellArrays c, Control* ctl, int
 }
 
 // max |u - Lambda(u)| over non-exit grid nodes (FP64), count of non-finite
-// values, largest finite value; then copy-out to the caller's layout.
-template <bool FINAL>
+// values, largest finite value, and the copy-out to the caller's layout.
+// MODE 0 (after the monotone polish) also records the residual as the
+// fallback check; MODE 1 is the final pass of the FP64 path; MODE 2 runs
+// only when the replace-mode fallback ran, and redoes MODE 0's final part.
+// Blocks take grid rows (fixed j, k) and threads the i of a row, so every
+// index is a shift or a 32-bit operation.
+template <int MODE>
 __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, int count,
-                                        Control* ctl) {
+                                        Control* ctl, double kappa) {
   const int ii = blockIdx.y;
   if (ii >= count) return;
+  if (MODE == 2 && (ctl->status || !fallback_needed(ctl, kappa))) return;
   const FinalInstance P = fi[ii];
   const double qb = q_base(ctl);
   const double* u = static_cast<const double*>(P.u64);
   const double* s = static_cast<const double*>(P.s64);
-  const int N = P.n, N3 = N * N * N;
-  const long long total = (long long)P.nx * P.ny * P.nz;
+  const int lg = __ffs(P.n) - 1, nm = P.n - 1;
+  const long long N3 = 1ll << (3 * lg);
   const long long sy = P.px64, sz = P.px64 * P.py;
+  const int rows = P.ny * P.nz;
   unsigned long long rmax = 0, umax = 0, nbad = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e % P.nx, j = (e / P.nx) % P.ny, k = e / ((long long)P.nx * P.ny);
-    const long long t = (i + 1) + sy * (j + 1) + sz * (k + 1);
-    const double v = u[t];
-    if (FINAL) P.out[e] = P.mask[e] ? P.q[e] : v + qb;
-    if (!isfinite(v)) {
-      ++nbad;
-      continue;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % P.ny, k = row / P.ny;
+    const long long rbase = (long long)row * P.nx;
+    const long long tbase = 1 + sy * (j + 1) + sz * (k + 1);
+    const long long cbase = (long long)P.ncx * ((j >> lg) + (long long)P.ncy * (k >> lg));
+    const int in_cell = ((j & nm) << lg) + ((k & nm) << (2 * lg));
+    for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
+      const long long t = tbase + i;
+      const double v = u[t];
+      const long long e = rbase + i;
+      P.out[e] = P.mask[e] ? P.q[e] : v + qb;
+      if (!isfinite(v)) {
+        ++nbad;
+        continue;
+      }
+      const unsigned long long o = ord_of_double(v);
+      umax = o > umax ? o : umax;
+      const double sv = s[(cbase + (i >> lg)) * N3 + (i & nm) + in_cell];
+      if (!(sv < CUDART_INF)) continue;  // exit node
+      const double ax = nmin(u[t - 1], u[t + 1]);
+      const double ay = nmin(u[t - sy], u[t + sy]);
+      const double az = nmin(u[t - sz], u[t + sz]);
+      const double lam = local_solve_direct(ax, ay, az, sv);
+      // A value left below the fixed point (lift too small) or above it (a
+      // flag skipped on the FP32 error bound) both show here and send the
+      // solve to the replace-mode fallback.
+      const double r = fabs(v - lam);
+      const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+      rmax = rb > rmax ? rb : rmax;
     }
-    const unsigned long long o = ord_of_double(v);
-    umax = o > umax ? o : umax;
-    const long long cx = i / N, cy = j / N, cz = k / N;
-    const long long lc = cx + P.ncx * (cy + (long long)P.ncy * cz);
-    const double sv = s[lc * N3 + (i % N) + N * ((j % N) + N * (k % N))];
-    if (!(sv < CUDART_INF)) continue;  // exit node
-    const double ax = nmin(u[t - 1], u[t + 1]);
-    const double ay = nmin(u[t - sy], u[t + sy]);
-    const double az = nmin(u[t - sz], u[t + sz]);
-    const double lam = local_solve_direct(ax, ay, az, sv);
-    // |u - Lambda(u)|: in the check pass, a value left below the fixed point
-    // (lift too small) or above it (a flag skipped on the FP32 error bound)
-    // both send the solve to the replace-mode fallback
-    const double r = fabs(v - lam);
-    const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
-    rmax = rb > rmax ? rb : rmax;
   }
-  block_max_u64(rmax, FINAL ? &ctl->resid_bits : &ctl->check_bits);
-  if (FINAL) {
-    block_max_u64(umax, &ctl->final_umax_bits);
-    for (int o = 16; o; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
-    if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(&ctl->nonfinite, nbad);
-  }
+  if (MODE == 0) block_max_u64(rmax, &ctl->check_bits);
+  block_max_u64(rmax, &ctl->resid_bits);
+  block_max_u64(umax, &ctl->final_umax_bits);
+  for (int o = 16; o; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+  if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(&ctl->nonfinite, nbad);
 }
 
 }  // namespace
@@ -529,12 +544,20 @@ cudaError_t launch_polish_prep(const PolishInstance* d_pi, int count, long long 
   return cudaGetLastError();
 }
 
+static dim3 row_grid(long long rows, int count, int sms) {
+  long long blocks = rows;
+  const long long cap = (long long)sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return dim3((unsigned)blocks, (unsigned)count, 1);
+}
+
 cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi, int count,
-                                 long long max_nodes, int max_cells, int total_cells,
+                                 long long max_rows, int max_cells, int total_cells,
                                  CellArrays cells, Control* ctl, double kappa, int sms,
                                  cudaStream_t st) {
-  residual_extract_kernel<false><<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_fi, count,
-                                                                                    ctl);
+  residual_extract_kernel<0><<<row_grid(max_rows, count, sms), 128, 0, st>>>(d_fi, count, ctl,
+                                                                             kappa);
   {
     long long blocks = ((long long)max_cells * 32 + 255) / 256;
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
@@ -548,10 +571,15 @@ cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_nodes,
-                                    Control* ctl, int sms, cudaStream_t st) {
-  residual_extract_kernel<true><<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_fi, count,
-                                                                                   ctl);
+cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_rows,
+                                    Control* ctl, bool after_fallback, double kappa, int sms,
+                                    cudaStream_t st) {
+  if (after_fallback)
+    residual_extract_kernel<2><<<row_grid(max_rows, count, sms), 128, 0, st>>>(d_fi, count, ctl,
+                                                                               kappa);
+  else
+    residual_extract_kernel<1><<<row_grid(max_rows, count, sms), 128, 0, st>>>(d_fi, count, ctl,
+                                                                               kappa);
   return cudaGetLastError();
 }
 

@@ -57,11 +57,15 @@ cudaError_t launch_polish_prep(const PolishInstance* d_pi, int count, long long 
                                long long max_nodes, int max_cells, int total_cells,
                                CellArrays cells, Control* ctl, int sms, cudaStream_t st);
 cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi, int count,
-                                 long long max_nodes, int max_cells, int total_cells,
+                                 long long max_rows, int max_cells, int total_cells,
                                  CellArrays cells, Control* ctl, double kappa, int sms,
                                  cudaStream_t st);
-cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_nodes,
-                                    Control* ctl, int sms, cudaStream_t st);
+// max_rows: the largest ny * nz of the launch.  after_fallback: the pass
+// after the replace-mode fallback (a no-op on the device unless it ran);
+// otherwise the final pass of the FP64 path.
+cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_rows,
+                                    Control* ctl, bool after_fallback, double kappa, int sms,
+                                    cudaStream_t st);
 
 // Persistent cell kernels (eik_cells_f32.cu / eik_cells_f64.cu).
 cudaError_t launch_cells(bool fp64, bool replace, int n, const CellKernelParams& p, int sms,

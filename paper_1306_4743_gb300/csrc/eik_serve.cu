@@ -28,9 +28,9 @@ constexpr int kMaxBatch = 64;
 struct Request {
   int64_t dims[3];
   double h, tol;
-  std::vector<float> F;
-  std::vector<uint8_t> mask;
-  std::vector<double> q;
+  const float* F;  // the caller's buffers, read until the ticket completes
+  const uint8_t* mask;
+  const double* q;
   double* u_out;
   double* staging;  // where the batch writes; u_out unless cancelled
   int state;        // 0 waiting, 1 on the device, 2 done
@@ -84,9 +84,9 @@ bool dims_ok(const int64_t* d) {
 }
 
 void release_inputs(Request* r) {
-  std::vector<float>().swap(r->F);
-  std::vector<uint8_t>().swap(r->mask);
-  std::vector<double>().swap(r->q);
+  r->F = nullptr;
+  r->mask = nullptr;
+  r->q = nullptr;
 }
 
 // Retire every batch whose stream has finished.
@@ -182,9 +182,9 @@ void admit(eik_ctx* ctx, ServeState* s) {
     std::vector<double*> U;
     for (uint64_t id : ids) {
       Request* r = s->req[id];
-      F.push_back(r->F.data());
-      M.push_back(r->mask.data());
-      Q.push_back(r->q.data());
+      F.push_back(r->F);
+      M.push_back(r->mask);
+      Q.push_back(r->q);
       U.push_back(r->staging);
       r->state = 1;
     }
@@ -225,13 +225,12 @@ int eik_submit(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
   }
   Request* r = new (std::nothrow) Request();
   if (!r) return EIK_ENOMEM;
-  const size_t nodes = (size_t)dims[0] * dims[1] * dims[2];
   memcpy(r->dims, dims, sizeof(r->dims));
   r->h = h;
   r->tol = tol;
-  r->F.assign(F, F + nodes);
-  r->mask.assign(src_mask, src_mask + nodes);
-  r->q.assign(q, q + nodes);
+  r->F = F;
+  r->mask = src_mask;
+  r->q = q;
   r->u_out = u_out;
   r->staging = u_out;
   r->state = 0;

@@ -12,6 +12,8 @@
 
 namespace eik {
 
+struct Launch;
+
 // Device and pinned host memory, stream and events of one batch in flight.
 struct Exec {
   cudaStream_t stream = nullptr;
@@ -22,7 +24,14 @@ struct Exec {
   size_t h_small_size = 0;
   char* h_out = nullptr;  // pinned: results of an asynchronous host-buffer batch
   size_t h_out_size = 0;
+  char* h_ctl = nullptr;  // pinned: read-back of the control block
+  size_t h_ctl_size = 0;
   cudaEvent_t ev[6] = {};
+  // captured launch sequence of the last device-buffer batch, replayed while
+  // its arguments (and so its arena layout and tensor maps) are unchanged
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned long long> graph_key;
+  Launch* graph_launch = nullptr;
 };
 
 // A launched batch, until eik_finish_batch has read it back.

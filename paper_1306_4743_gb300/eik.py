@@ -33,7 +33,7 @@ PRECISIONS = {"fp64": 0, "fp32_polish": 1}
 EXPORTED = ("eik_opts_default", "eik_create", "eik_destroy", "eik_strerror",
             "eik_solve", "eik_solve_device", "eik_solve_batch",
             "eik_solve_batch_device", "eik_submit", "eik_poll", "eik_cancel",
-            "eik_solve_device_noalloc")
+            "eik_solve_device_noalloc", "eik_autotune", "eik_struct_sizes")
 
 
 class Opts(ctypes.Structure):
@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
                 ("bucket_width", ctypes.c_double),
                 ("max_sweeps_per_visit", ctypes.c_int),
                 ("queue_order", ctypes.c_int),
-                ("bulk_kappa_rel", ctypes.c_double)]
+                ("bulk_kappa_rel", ctypes.c_double),
+                ("use_graphs", ctypes.c_int), ("reserved3", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -65,7 +66,9 @@ class Stats(ctypes.Structure):
                 ("busy_seconds_bulk", ctypes.c_double),
                 ("busy_seconds_polish", ctypes.c_double),
                 ("fallback_visits", ctypes.c_uint64),
-                ("phase_seconds", (ctypes.c_double * 4) * 2)]
+                ("phase_seconds", (ctypes.c_double * 4) * 2),
+                ("revisits", ctypes.c_uint64 * 2),
+                ("max_visit_sweeps", ctypes.c_uint64 * 3)]
 
     def as_dict(self):
         d = {}
@@ -73,6 +76,8 @@ class Stats(ctypes.Structure):
             v = getattr(self, name)
             if name == "phase_seconds":
                 v = [[v[i][j] for j in range(4)] for i in range(2)]
+            elif name in ("revisits", "max_visit_sweeps"):
+                v = [int(x) for x in v]
             d[name] = v
         return d
 
@@ -120,9 +125,18 @@ def load(path: str | None = None):
     lib.eik_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(Stats)]
     lib.eik_cancel.argtypes = [P, ctypes.c_uint64]
     lib.eik_solve_device_noalloc.argtypes = [P, D, P, P, P, D, P, P, ctypes.POINTER(Stats)]
+    lib.eik_autotune.argtypes = [P, P, D, P, P, P, D, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.eik_struct_sizes.argtypes = [ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]
     for name in EXPORTED:
         if name != "eik_strerror":
             getattr(lib, name).restype = I
+    so, ss = ctypes.c_size_t(), ctypes.c_size_t()
+    lib.eik_struct_sizes(ctypes.byref(so), ctypes.byref(ss))
+    if (so.value, ss.value) != (ctypes.sizeof(Opts), ctypes.sizeof(Stats)):
+        raise RuntimeError("libeik struct sizes %d/%d differ from the binding's %d/%d: "
+                           "rebuild the library" % (so.value, ss.value, ctypes.sizeof(Opts),
+                                                    ctypes.sizeof(Stats)))
     if path == LIB_PATH or _lib is None:
         _lib = lib
     return lib
@@ -136,7 +150,7 @@ def default_opts() -> Opts:
 
 def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
               spin_cap_us=None, bucket_width=None, max_sweeps_per_visit=None, max_ctas=0,
-              bulk_kappa_rel=None, queue_order=None) -> Opts:
+              bulk_kappa_rel=None, queue_order=None, use_graphs=None) -> Opts:
     """eik_opts from the library defaults with the given fields changed
     (None = keep the default)."""
     o = default_opts()
@@ -155,6 +169,8 @@ def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
         o.bulk_kappa_rel = float(bulk_kappa_rel)
     if queue_order is not None:
         o.queue_order = int(queue_order)
+    if use_graphs is not None:
+        o.use_graphs = int(use_graphs)
     return o
 
 
@@ -184,14 +200,14 @@ class Solver:
     def __init__(self, precision="fp32_polish", cell_n=0, device=0,
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
                  max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
-                 queue_order=None):
+                 queue_order=None, use_graphs=None):
         """Options left at None keep the library defaults (eik_opts_default)."""
         self.lib = load()
         o = make_opts(precision=precision, cell_n=cell_n, device=device,
                       hbm_budget_bytes=hbm_budget_bytes, spin_cap_us=spin_cap_us,
                       bucket_width=bucket_width, max_sweeps_per_visit=max_sweeps_per_visit,
                       max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
-                      queue_order=queue_order)
+                      queue_order=queue_order, use_graphs=use_graphs)
         self.opts = o
         self._outputs = {}  # ticket -> output array, alive until done or cancelled
         self.ctx = ctypes.c_void_p()
@@ -249,6 +265,18 @@ class Solver:
         d["status"] = rc
         return u, d
 
+    def autotune(self, F, mask, q, h, tol=0.0):
+        """Pick cell size and cell-kernel CTAs for grids of this size
+        (eik_autotune); returns (cell_n, ctas)."""
+        F_h, m_h, q_h = _host_arrays(F, mask, q)
+        bn, bc = ctypes.c_int(0), ctypes.c_int(0)
+        rc = self.lib.eik_autotune(self.ctx, _dims_of(F_h.shape), float(h), F_h.ctypes.data,
+                                   m_h.ctypes.data, q_h.ctypes.data, float(tol),
+                                   ctypes.byref(bn), ctypes.byref(bc))
+        if rc != EIK_OK:
+            raise EikError(rc, "eik_autotune")
+        return bn.value, bc.value
+
     # -- many grids in one launch -------------------------------------------
     def solve_batch(self, problems, tol=0.0, check=True):
         """problems: list of (F, mask, q, h) numpy tuples.  Returns (list of u, stats)."""
@@ -302,8 +330,8 @@ class Solver:
     # -- serving ------------------------------------------------------------
     def submit(self, F, mask, q, h, tol=0.0, out=None):
         """Queue one solve; returns (ticket, out array filled on completion).
-        The binding keeps the output array alive until the ticket is done or
-        cancelled (the library writes into it asynchronously)."""
+        The binding keeps the input and output arrays alive until the ticket
+        is done or cancelled (the library uses them asynchronously)."""
         F_h, m_h, q_h = _host_arrays(F, mask, q)
         u = out if out is not None else np.empty(F_h.shape, dtype=np.float64)
         if not (u.flags.c_contiguous and u.dtype == np.float64 and u.shape == F_h.shape):
@@ -314,7 +342,8 @@ class Solver:
                                  ctypes.byref(t))
         if rc != EIK_OK:
             raise EikError(rc, "eik_submit")
-        self._outputs[t.value] = u
+        # the library reads the inputs and writes u until the ticket is done
+        self._outputs[t.value] = (u, F_h, m_h, q_h)
         return t.value, u
 
     def poll(self, ticket):

@@ -34,11 +34,20 @@ def test_defaults_and_strerror_without_gpu():
     from paper_1306_4743_gb300 import eik
     o = eik.default_opts()
     assert o.precision == 1 and o.cell_n == 0 and o.spin_cap_us == 5_000_000
-    assert o.max_sweeps_per_visit == 4096 and o.bucket_width == 0.5 and o.queue_order == 1
+    assert o.max_sweeps_per_visit == 4096 and o.bucket_width == 0.25 and o.queue_order == 1
     lib = eik.load()
     assert lib.eik_strerror(0) == b"ok"
     assert lib.eik_strerror(5).startswith(b"device wait")
     assert lib.eik_strerror(12345) == b"unknown status"
+
+
+def test_struct_mirrors_match_the_library():
+    from paper_1306_4743_gb300 import eik
+    lib = eik.load()
+    so, ss = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.eik_struct_sizes(ctypes.byref(so), ctypes.byref(ss)) == 0
+    assert so.value == ctypes.sizeof(eik.Opts) and ss.value == ctypes.sizeof(eik.Stats)
+    assert lib.eik_struct_sizes(None, None) == 0
 
 
 def test_create_fails_cleanly_without_gpu():

@@ -165,3 +165,27 @@ def test_invalid_inputs(eik):
         # the context is still usable after rejected calls
         u, st = s.solve(F, mask, q, 0.1)
         assert st["status"] == 0 and u[0, 0, 0] == 0.0
+
+
+# The paper's other workloads (Sec. 6): the rapidly oscillating and the
+# strongly curved speeds with the even-grid 8-node exit set, the two
+# checkerboards, and the permeable shell maze whose F jumps by 1000x across
+# surfaces that cut through cells.
+PAPER_WORKLOADS = {
+    "ex1_64": lambda: W.paper_example(1, 64),
+    "ex2_96": lambda: W.paper_example(2, 96),
+    "ex3_80": lambda: W.paper_example(3, 80),
+    "checker11_88": lambda: W.checkerboard(88, 11),
+    "checker41_84": lambda: W.checkerboard(84, 41),
+    "maze_64": lambda: W.shell_maze(64),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
+@pytest.mark.parametrize("name", sorted(PAPER_WORKLOADS))
+def test_paper_workloads(eik, precision, name):
+    p = PAPER_WORKLOADS[name]()
+    with eik.Solver(precision=precision) as s:
+        u, st = s.solve(p.F, p.mask, p.q, p.h)
+    check_against_oracle(u, p, precision)
+    assert st["nonfinite"] == 0

@@ -97,7 +97,12 @@ typedef struct {
   int use_graphs;           /* eik_solve_batch_device: capture the launch
                                sequence as a CUDA graph and replay it while
                                the arguments repeat (default 1) */
-  int reserved3;            /* must be 0 */
+  int cell_key;             /* cell value a flag gives the neighbour cell:
+                               0 = Eq. 3, the smallest flagging border value
+                               (default); 1 = Eq. 4, the largest one plus
+                               (n + 1) h / 2 over the speed at the neighbour's
+                               centre, with cell values kept (not reset to
+                               +inf) when a cell is taken (Sec. 7) */
 } eik_opts;
 
 /* Counters and results of one solve (of the whole batch for batch calls). */

@@ -490,6 +490,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.kappa_from_ctl = polish ? 1 : 0;
   p.relaxed = ctx->opts.queue_order;
   p.gated = 0;
+  p.cell_key = ctx->opts.cell_key;
   CK(cudaEventRecord(ex.ev[1], st));
   int grid_ctas = 0;
   CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas));
@@ -718,7 +719,9 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
   }
   if (o.precision != EIK_FP64 && o.precision != EIK_FP32_POLISH) return EIK_EINVAL;
   if (o.cell_n != 0 && size_index(o.cell_n) < 0) return EIK_EINVAL;
-  if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1 || o.reserved3) return EIK_EINVAL;
+  if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1 || o.cell_key < 0 ||
+      o.cell_key > 1)
+    return EIK_EINVAL;
   if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
   if (!(o.bulk_kappa_rel >= 0.0) || isinf(o.bulk_kappa_rel)) return EIK_EINVAL;
   if (!(o.bucket_width > 0.0)) o.bucket_width = 0.25;

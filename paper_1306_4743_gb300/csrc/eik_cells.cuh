@@ -39,8 +39,11 @@ __device__ __forceinline__ bool vlt(float a, float b) { return a < b; }
 __device__ __forceinline__ bool vlt(double a, double b) { return dlt_nn(a, b); }
 
 // Per-node bits of the staged cell: written back, changed by more than
-// kappa (flags the neighbour cell), active (to be recomputed, Alg. 2).
-constexpr unsigned char kWritten = 1, kBig = 2, kActive = 4;
+// kappa (flags the neighbour cell), active (to be recomputed, Alg. 2).  One
+// 32-bit word per node: sub-word shared-memory accesses cost about twice
+// the latency of word accesses, and these bits sit on the sweep's
+// critical path.
+constexpr unsigned kWritten = 1, kBig = 2, kActive = 4;
 
 template <typename T, int N>
 struct Geo {
@@ -53,6 +56,19 @@ struct Geo {
   static constexpr int SZ = BX * BY;
   static constexpr int N3 = N * N * N;
   static constexpr int NPLANES = 3 * (N - 1) + 1;
+  // most nodes on one plane i + j + k = C
+  static constexpr int max_plane() {
+    int best = 0;
+    for (int C = 0; C < NPLANES; ++C) {
+      int c = 0;
+      for (int b = 0; b < N; ++b)
+        for (int a = 0; a < N; ++a)
+          if (C - a - b >= 0 && C - a - b < N) ++c;
+      best = c > best ? c : best;
+    }
+    return best;
+  }
+  static constexpr int MAXPLANE = max_plane();
   static constexpr int UBYTES = BX * BY * BZ * ES;
   static constexpr int SBYTES = N3 * ES;
   static constexpr int align128(int b) { return (b + 127) / 128 * 128; }
@@ -61,7 +77,7 @@ struct Geo {
   static constexpr int OFF_S = align128(UBYTES);
   static constexpr int OFF_CHG = OFF_S + align128(SBYTES);
   // active-node list of one plane (at most N^2 nodes lie on a plane)
-  static constexpr int OFF_LIST = OFF_CHG + align128(N3);
+  static constexpr int OFF_LIST = OFF_CHG + align128(N3 * 4);
   static constexpr int OFF_BAR = OFF_LIST + align128(N * N * 2);
   static constexpr int WORKER_BYTES = OFF_BAR + 128;
   // CTA-wide: plane table | plane offsets
@@ -95,13 +111,13 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
 // the sweep has just left.
 template <typename T, int N, bool REPLACE>
 __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
-                                            unsigned char* __restrict__ chg, int i, int j, int k,
+                                            unsigned* __restrict__ chg, int i, int j, int k,
                                             int fx, int fy, int fz, T kappa,
                                             unsigned& n_updates, unsigned& left) {
   using G = Geo<T, N>;
   const int si = i + N * (j + N * k);
   const T s = S[si];
-  unsigned char c1 = chg[si] & (unsigned char)~kActive;  // Alg. 2 l.4
+  unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
   if (s < tinf<T>()) {
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
     const T v = U[t];
@@ -178,7 +194,7 @@ __device__ __forceinline__ unsigned worker_or3(int worker, unsigned bits) {
 // active node; first > last when no node is active.  `ws` is 2 * WPC ints
 // of worker scratch.
 template <int N, int WPC>
-__device__ __forceinline__ void active_planes(const unsigned char* __restrict__ chg, int dir,
+__device__ __forceinline__ void active_planes(const unsigned* __restrict__ chg, int dir,
                                               int tid, int worker, int* ws, int& first,
                                               int& last) {
   constexpr int NT = WPC * 32, N3 = N * N * N;
@@ -186,20 +202,16 @@ __device__ __forceinline__ void active_planes(const unsigned char* __restrict__ 
   const int fy = (dir & 2) ? N - 1 : 0;
   const int fz = (dir & 4) ? N - 1 : 0;
   int lo = 1 << 20, hi = -1;
-  for (int e = tid * 16; e < N3; e += NT * 16) {
+  for (int e = tid * 4; e < N3; e += NT * 4) {
     const uint4 w = *reinterpret_cast<const uint4*>(chg + e);
     const unsigned wd[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      unsigned act = wd[q] & 0x04040404u;
-      while (act) {
-        const int b = (__ffs(act) - 1) >> 3;
-        act &= act - 1u;
-        const int idx = e + 4 * q + b;
-        const int pl = ((idx % N) ^ fx) + (((idx / N) % N) ^ fy) + ((idx / (N * N)) ^ fz);
-        lo = pl < lo ? pl : lo;
-        hi = pl > hi ? pl : hi;
-      }
+      if (!(wd[q] & kActive)) continue;
+      const int idx = e + q;
+      const int pl = ((idx % N) ^ fx) + (((idx / N) % N) ^ fy) + ((idx / (N * N)) ^ fz);
+      lo = pl < lo ? pl : lo;
+      hi = pl > hi ? pl : hi;
     }
   }
   lo = __reduce_min_sync(0xffffffffu, lo);
@@ -239,7 +251,7 @@ __device__ __forceinline__ void active_planes(const unsigned char* __restrict__ 
 // however few lanes are active.
 template <typename T, int N, int WPC, bool REPLACE, bool COMPACT>
 __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __restrict__ S,
-                                               unsigned char* __restrict__ chg,
+                                               unsigned* __restrict__ chg,
                                                const unsigned short* __restrict__ tab,
                                                const int* __restrict__ off,
                                                unsigned short* __restrict__ list, int dir,
@@ -247,32 +259,52 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
                                                T kappa, unsigned& n_updates) {
   using G = Geo<T, N>;
   constexpr int NT = WPC * 32;
+  // Nodes of one plane do not depend on each other: a thread takes up to UNR
+  // of them, so their loads and arithmetic overlap; every plane fits.
+  constexpr int UNR = (N >= 16 && WPC == 1) ? 6 : 2;
+  static_assert(G::MAXPLANE <= UNR * NT, "a plane must fit one pass of the worker");
   static_assert(!COMPACT || WPC == 1, "the gathered list is per warp");
+  constexpr unsigned kNone = 0xffffu;  // packed entries use 15 bits
   const int fx = (dir & 1) ? N - 1 : 0;
   const int fy = (dir & 2) ? N - 1 : 0;
   const int fz = (dir & 4) ? N - 1 : 0;
+  // The plane table entries of the next plane are loaded while the current
+  // one is swept, so that after a plane's barrier only the active bits are
+  // still to be read.
+  unsigned nxt[UNR];
+  {
+    const int b0 = off[first], e1 = off[first + 1];
+#pragma unroll
+    for (int h = 0; h < UNR; ++h) {
+      const int e = b0 + tid + h * NT;
+      nxt[h] = e < e1 ? (unsigned)tab[e] : kNone;
+    }
+  }
   unsigned left = 0;
   for (int C = first; C < G::NPLANES; ++C) {
-    const int beg = off[C], end = off[C + 1];
-    // Nodes of one plane do not depend on each other: each thread takes UNR
-    // per pass, so their loads and arithmetic overlap.
-    constexpr int UNR = (N >= 16 && WPC == 1) ? 3 : 2;
+    unsigned cur[UNR];
+#pragma unroll
+    for (int h = 0; h < UNR; ++h) cur[h] = nxt[h];
+    if (C + 1 < G::NPLANES) {
+      const int b0 = off[C + 1], e1 = off[C + 2];
+#pragma unroll
+      for (int h = 0; h < UNR; ++h) {
+        const int e = b0 + tid + h * NT;
+        nxt[h] = e < e1 ? (unsigned)tab[e] : kNone;
+      }
+    }
     bool any;
     if constexpr (!COMPACT) {
       bool did = false;
-      for (int e0 = beg + tid; e0 < end; e0 += UNR * NT) {
 #pragma unroll
-        for (int h = 0; h < UNR; ++h) {
-          const int e = e0 + h * NT;
-          if (e >= end) break;
-          const unsigned pk = tab[e];
-          const int i = (int)(pk & 31u) ^ fx;
-          const int j = (int)((pk >> 5) & 31u) ^ fy;
-          const int k = (int)((pk >> 10) & 31u) ^ fz;
-          if (!(chg[i + N * (j + N * k)] & kActive)) continue;  // Alg. 2 l.1-2
-          did = true;
-          update_node<T, N, REPLACE>(U, S, chg, i, j, k, fx, fy, fz, kappa, n_updates, left);
-        }
+      for (int h = 0; h < UNR; ++h) {
+        if (cur[h] == kNone) continue;
+        const int i = (int)(cur[h] & 31u) ^ fx;
+        const int j = (int)((cur[h] >> 5) & 31u) ^ fy;
+        const int k = (int)((cur[h] >> 10) & 31u) ^ fz;
+        if (!(chg[i + N * (j + N * k)] & kActive)) continue;  // Alg. 2 l.1-2
+        did = true;
+        update_node<T, N, REPLACE>(U, S, chg, i, j, k, fx, fy, fz, kappa, n_updates, left);
       }
       any = worker_any<WPC>(worker, did);  // also ends the plane
     } else {
@@ -280,14 +312,13 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
       const int lane = tid & 31;
       const unsigned below = (1u << lane) - 1u;
       int total = 0;
-      for (int e0 = beg; e0 < end; e0 += 32) {
-        const int e = e0 + lane;
+#pragma unroll
+      for (int h = 0; h < UNR; ++h) {
         bool act = false;
         unsigned pk = 0;
-        if (e < end) {
-          const unsigned q = tab[e];
-          const int i = (int)(q & 31u) ^ fx, j = (int)((q >> 5) & 31u) ^ fy,
-                    k = (int)((q >> 10) & 31u) ^ fz;
+        if (cur[h] != kNone) {
+          const int i = (int)(cur[h] & 31u) ^ fx, j = (int)((cur[h] >> 5) & 31u) ^ fy,
+                    k = (int)((cur[h] >> 10) & 31u) ^ fz;
           act = (chg[i + N * (j + N * k)] & kActive) != 0;
           pk = (unsigned)i | ((unsigned)j << 5) | ((unsigned)k << 10);
         }
@@ -333,7 +364,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   unsigned char* wbase = smem + G::HEAD_BYTES + worker * G::WORKER_BYTES;
   T* U = reinterpret_cast<T*>(wbase);
   T* S = reinterpret_cast<T*>(wbase + G::OFF_S);
-  unsigned char* chg = wbase + G::OFF_CHG;
+  unsigned* chg = reinterpret_cast<unsigned*>(wbase + G::OFF_CHG);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(wbase + G::OFF_BAR);
   // scratch: [0] cell, [1] direction word, [2..7] face keys, [12..19] plane range
   int* wshared = reinterpret_cast<int*>(wbase + G::OFF_BAR + 16);
@@ -363,7 +394,8 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     if (wwarp == 0) {
       cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane, &slot, p.relaxed != 0);
       if (lane == 0 && cell >= 0) {
-        atomicExch(cells.key + cell, kKeyInf);        // V^c <- +inf (Alg. 1 l.5)
+        // V^c <- +inf (Alg. 1 l.5); the Eq. 4 variant keeps it (Sec. 7)
+        if (p.cell_key == 0) atomicExch(cells.key + cell, kKeyInf);
         pref = atomicAnd(cells.dir + cell, kDirVisited);  // take dirs and faces
       }
       pref = __shfl_sync(0xffffffffu, pref, 0);
@@ -410,8 +442,8 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     const bool revisit = (pref & kDirVisited) != 0;
     const unsigned faces = (pref >> kFaceShift) & 0x3fu;
     {
-      const unsigned fill = revisit ? 0u : 0x04040404u;
-      for (int e = tid * 16; e < G::N3; e += NT * 16)
+      const unsigned fill = revisit ? 0u : (unsigned)kActive;
+      for (int e = tid * 4; e < G::N3; e += NT * 4)
         *reinterpret_cast<uint4*>(chg + e) = make_uint4(fill, fill, fill, fill);
     }
     {
@@ -512,7 +544,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       const int axis = f >> 1, upper = f & 1;
       const int ncoord = (axis == 0 ? cx : axis == 1 ? cy : cz) + (upper ? 1 : -1);
       const int nlim = axis == 0 ? I.ncx : axis == 1 ? I.ncy : I.ncz;
-      unsigned m = 0xffffffffu;
+      unsigned m = 0xffffffffu, mx = 0u;  // smallest / largest key of the flagging values
       if (ncoord >= 0 && ncoord < nlim) {  // warp-uniform
         for (int q = lane; q < N * N; q += 32) {
           const int a = q % N, b = q / N;
@@ -533,10 +565,29 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
             if (REPLACE || vi < vj) {
               const unsigned kk = key_of(vi);
               m = kk < m ? kk : m;
+              mx = kk > mx ? kk : mx;
             }
           }
         }
         m = __reduce_min_sync(0xffffffffu, m);
+        if (p.cell_key == 1) {
+          // Eq. 4: the largest flagging value plus the travel time over half
+          // a cell and a node, (n h + h) / 2, at the speed of the
+          // neighbour's centre node: (n + 1) / 2 times its s = h / F.
+          mx = __reduce_max_sync(0xffffffffu, mx);
+          if (lane == 0 && m != 0xffffffffu) {
+            const int nlc = axis == 0 ? lc + (upper ? 1 : -1)
+                          : axis == 1 ? lc + (upper ? I.ncx : -I.ncx)
+                                      : lc + (upper ? I.ncx * I.ncy : -I.ncx * I.ncy);
+            const int bx = nlc % I.ncx, by = (nlc / I.ncx) % I.ncy, bz = nlc / (I.ncx * I.ncy);
+            // centre of the cell's nodes inside the grid (edge cells are partial)
+            const int ci = min(N, I.nx - N * bx) / 2, cj = min(N, I.ny - N * by) / 2,
+                      ck = min(N, I.nz - N * bz) / 2;
+            const T sc = static_cast<const T*>(I.s)[(size_t)nlc * G::N3 + ci + N * (cj + N * ck)];
+            if (sc < tinf<T>())  // an exit node at the centre keeps the Eq. 3 value
+              m = key_of((float)(float_of_ord(mx) + 0.5f * (float)(N + 1) * (float)sc));
+          }
+        }
       }
       if (lane == 0) fkey[f] = m;
     }

@@ -119,6 +119,7 @@ struct CellKernelParams {
   int kappa_from_ctl;               // 1: take kappa from ctl->kappa_bulk
   int relaxed;                      // 1: move past a bucket once its stack is empty
   int gated;                        // 1: polish schedule (cells wait for deps == 0)
+  int cell_key;                     // 0: Eq. 3 cell values, 1: Eq. 4 (no reset on pop)
 };
 
 }  // namespace eik

@@ -274,6 +274,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.kappa_from_ctl = 0;
   p.relaxed = 1;
   p.gated = 0;
+  p.cell_key = 0;
   int grid = 0;
   CKN(launch_cells(true, false, n, p, slot->sms, st, &grid));
   CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), 1,

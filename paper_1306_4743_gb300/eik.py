@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
                 ("max_sweeps_per_visit", ctypes.c_int),
                 ("queue_order", ctypes.c_int),
                 ("bulk_kappa_rel", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("reserved3", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("cell_key", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -150,7 +150,8 @@ def default_opts() -> Opts:
 
 def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
               spin_cap_us=None, bucket_width=None, max_sweeps_per_visit=None, max_ctas=0,
-              bulk_kappa_rel=None, queue_order=None, use_graphs=None) -> Opts:
+              bulk_kappa_rel=None, queue_order=None, use_graphs=None,
+              cell_key=None) -> Opts:
     """eik_opts from the library defaults with the given fields changed
     (None = keep the default)."""
     o = default_opts()
@@ -171,6 +172,8 @@ def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
         o.queue_order = int(queue_order)
     if use_graphs is not None:
         o.use_graphs = int(use_graphs)
+    if cell_key is not None:
+        o.cell_key = int(cell_key)
     return o
 
 
@@ -200,14 +203,14 @@ class Solver:
     def __init__(self, precision="fp32_polish", cell_n=0, device=0,
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
                  max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
-                 queue_order=None, use_graphs=None):
+                 queue_order=None, use_graphs=None, cell_key=None):
         """Options left at None keep the library defaults (eik_opts_default)."""
         self.lib = load()
         o = make_opts(precision=precision, cell_n=cell_n, device=device,
                       hbm_budget_bytes=hbm_budget_bytes, spin_cap_us=spin_cap_us,
                       bucket_width=bucket_width, max_sweeps_per_visit=max_sweeps_per_visit,
                       max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
-                      queue_order=queue_order, use_graphs=use_graphs)
+                      queue_order=queue_order, use_graphs=use_graphs, cell_key=cell_key)
         self.opts = o
         self._outputs = {}  # ticket -> output array, alive until done or cancelled
         self.ctx = ctypes.c_void_p()

@@ -432,6 +432,34 @@ def run_ours(args):
             "nodes_per_s": p.nodes / statistics.mean(ts), "ms": statistics.mean(ts) * 1e3,
             "max_rel_err_vs_oracle": (float(np.max(np.abs(u64.cpu().numpy() - ref)) / np.max(ref))
                                       if cpu is not None else None)}
+        # early termination (Sec. 6.4): error against the oracle and time per kappa
+        if cpu is not None:
+            sweep = []
+            for kap in (0.0, 1e-14, 1e-12, 1e-10, 1e-8, 1e-6):
+                row = {"tol": kap}
+                for prec in ("fp32_polish", "fp64"):
+                    uk = torch.empty_like(u_d)
+                    with eik.Solver(precision=prec, device=local) as sk:
+                        sk.solve(F_d, m_d, q_d, p.h, tol=kap, out=uk)
+                        ts = []
+                        for _ in range(2):
+                            flush.fill_(1.0)
+                            _, st = sk.solve(F_d, m_d, q_d, p.h, tol=kap, out=uk)
+                            ts.append(st["seconds"])
+                    row[prec] = {"ms": statistics.mean(ts) * 1e3,
+                                 "max_rel_err_vs_oracle":
+                                     float(np.max(np.abs(uk.cpu().numpy() - ref)) / np.max(ref))}
+                sweep.append(row)
+            extras["kappa_sweep"] = sweep
+        # the paper's synchronous comparator: whole-grid plane-parallel sweeping
+        ud = torch.empty_like(u_d)
+        eik.dfsm_solve(F_d, m_d, q_d, p.h, tol=args.tol, out=ud)
+        _, std = eik.dfsm_solve(F_d, m_d, q_d, p.h, tol=args.tol, out=ud)
+        extras["dfsm_single_instance"] = {
+            "nodes_per_s": p.nodes / std["seconds"], "ms": std["seconds"] * 1e3,
+            "sweeps": std["sweeps"],
+            "max_rel_err_vs_oracle": (float(np.max(np.abs(ud.cpu().numpy() - ref)) / np.max(ref))
+                                      if cpu is not None else None)}
         extras["serving"] = run_serving(eik, W, local, args.serve_requests,
                                         args.serve_unique, tol=args.tol,
                                         check=cpu is not None)

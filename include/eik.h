@@ -285,6 +285,50 @@ int eik_solve_device_noalloc(const int64_t dims[3], double h, const float *F_dev
                              double tol, double *u_out_dev, void *stream,
                              eik_stats *stats);
 
+/*
+ * Whole-grid sweeping baseline (the paper's parallel comparator DFSM,
+ * Sec. 2-3 and Tables 4-6): Fast Sweeping of the whole grid in the 8
+ * directions of the standard order, each direction over the planes
+ * i + j + k = C of that direction with the nodes of a plane updated in
+ * parallel, in FP64, until a sweep lowers no value by more than tol (tol = 0:
+ * until no value changes).  Same problem and arguments as eik_solve_device
+ * (device pointers, layout (nz, ny, nx), i fastest; u_out_dev caller-owned),
+ * plus max_sweeps (1 .. 2^20).  On success *sweeps (nullable) is the number
+ * of sweeps, and changed_per_sweep / max_drop_per_sweep (host arrays of
+ * max_sweeps entries, nullable) the count of values lowered by more than
+ * tol in each sweep and the largest such decrease.  Allocates its working
+ * memory (~16 B per node) for the call and frees it; runs on the current
+ * device and stream and synchronises the stream.  EIK_EINVAL for bad
+ * arguments, F <= 0 or non-finite, non-finite q, or no exit node;
+ * EIK_ENOMEM; EIK_ENOCONV when the last allowed sweep still changed a
+ * value (u_out holds that iterate); EIK_ETIMEOUT if a device-wide barrier
+ * waits longer than 5 s; EIK_ECUDA.
+ */
+int eik_dfsm_solve_device(const int64_t dims[3], double h, const float *F_dev,
+                          const uint8_t *src_mask_dev, const double *q_dev, double tol,
+                          int64_t max_sweeps, double *u_out_dev, void *stream,
+                          int64_t *sweeps, int64_t *changed_per_sweep,
+                          double *max_drop_per_sweep, eik_stats *stats);
+
+/*
+ * Diagnostic: accuracy of the device local solve of Eq. 2 used
+ * by the FP64 sweeps, against the direct FP64 evaluation of the same root
+ * (shifted closed forms with an FP64 square root, the form the residual
+ * certificate uses), on `count` inputs drawn on the device from a
+ * counter-based generator keyed by `seed`: s = h / F with h log-uniform in
+ * [2^-10, 2^-4] and F uniform in [0.05, 2], neighbour values a base uniform
+ * in [0, 2) plus offsets uniform in [0, 2s] (one in eight +inf), so that the
+ * one-, two- and three-term cases all occur.  On success *max_ulps is the
+ * largest difference in units in the last place of the direct result and
+ * *max_rel the largest difference in units of (one ulp of the direct
+ * result + 2^-44 s), the accuracy the sweeps' solve is built for.  Runs on `device`, allocates
+ * and frees a few bytes of device memory, synchronises the device.
+ * Returns EIK_EINVAL for count < 1 or NULL outputs, EIK_ECUDA on a CUDA
+ * error.
+ */
+int eik_selftest_local_solve(int device, int64_t count, uint64_t seed, double *max_ulps,
+                             double *max_rel);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,13 +124,16 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
     const T xm = U[t - 1], xp = U[t + 1];
     const T ym = U[t - G::SY], yp = U[t + G::SY];
     const T zm = U[t - G::SZ], zp = U[t + G::SZ];
-    const T vk = v - kappa;  // off the solve's dependency chain
     const T nv = local_solve(nmin(xm, xp), nmin(ym, yp), nmin(zm, zp), s);
     ++n_updates;
     bool big;
     if constexpr (!REPLACE) {
       const bool lower = vlt(nv, v);
-      big = vlt(nv, vk);
+      if constexpr (sizeof(T) == 8) {
+        big = drop_exceeds(nv, v, (float)kappa);
+      } else {
+        big = vlt(nv, v - kappa);
+      }
       if (lower) {
         U[t] = nv;
         c1 |= big ? 3 : 1;

@@ -240,44 +240,138 @@ __device__ __forceinline__ double f64_of_f32_nn(float x) {
 }
 __device__ __forceinline__ bool dlt_nn(double a, double b) { return dbits(a) < dbits(b); }
 
+// A double x >= 0 as hi + lo with hi its leading 24 mantissa bits (the
+// truncation f32_of_f64_nn) and lo the remaining 29 bits rounded to a float:
+// x = hi + lo to about 2^-48 relative.  Integer pipe and one int -> float
+// conversion; no FP64 instruction.  Values below 2^-74 give lo = 0.
+__device__ __forceinline__ void split_nn(double x, float& hi, float& lo) {
+  hi = f32_of_f64_nn(x);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(b >> 52);
+  const unsigned low = (unsigned)(b & 0x1fffffffull);  // bits below the float mantissa
+  // low * 2^(e - 1075), the scale built as a float power of two
+  const int pe = e - 1075 + 127;
+  lo = (pe >= 1 && pe <= 254 && e < 2047) ? __uint2float_rn(low) * __int_as_float(pe << 23)
+                                           : 0.0f;
+}
+
+// a + b = s + t exactly (Knuth's two-sum), FP32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// a double from a float of either sign, on the integer pipe (0 for float
+// subnormals, which only arise as negligible corrections here).
+__device__ __forceinline__ double f64_of_f32(float x) {
+  const double m = f64_of_f32_nn(fabsf(x));
+  return __longlong_as_double(__double_as_longlong(m) |
+                              ((long long)(__float_as_uint(x) & 0x80000000u) << 32));
+}
+
 // FP64 local solve used by the sweeps: the shifted root w = U - a1 of
-//   f(w) = sum_{d<=m} (w - b_d)^2 - s^2 = 0,   b_d = a_d - a1,
+//   f(w) = sum_{d<=m} (w - b_d)^2 - s^2 = 0,   b_1 = 0, b_d = a_d - a1,
 // is first found in FP32 (term count m, and w32 to ~1e-7 relative), then
-// refined by one Newton step in FP64:  U = (a1 + w32) - f(w32) / f'(w32),
-// with f'(w) = 2 sum_{d<=m} (w - b_d) >= 2w >= 2s/sqrt(3).  Newton's error
-// after one step is ~ m e0^2 / f', i.e. ~1e-14 s, below an FP64 ulp of U;
-// f' only scales the tiny correction, so 1/f' is taken in FP32.  The
-// one-term root is exact (U = a1 + s).  Near a branch boundary the m-term
+// refined by one step:  U = (a1 + w32) + delta with delta from f(w32) and
+// f'(w) = 2 sum_{d<=m} (w - b_d) >= 2w >= 2s/sqrt(3) (newton_step: Newton
+// plus the second-order term, since f is quadratic; a plain Newton step
+// would leave m e0^2 / f' ~ 2^-41 s).  The one-term root is exact
+// (U = a1 + s).  Near a branch boundary the m-term
 // roots of both branches agree to O(e0^2 / s), so the FP32 choice of m
-// costs nothing.  The FP64 part is four dependent operations deep on the
-// two- and three-term paths (b_d, then r_d and a1 + w, then f, then U).
+// costs nothing.
+//
+// f(w32) is a small difference of O(s^2) terms, so it is evaluated with
+// error-free FP32 transformations instead of FP64 arithmetic: with b_d and
+// s split into float pairs (hi + lo), w32 - hi(b_d) and every square are
+// formed exactly (two-sum, FMA), the large terms are summed exactly, and
+// the lo parts enter through their first- and second-order terms.  f then
+// carries an error of ~2^-48 s^2, below what the FP64 result can resolve.
+// On this GPU an FP64 warp instruction occupies a scheduler's FP64 unit
+// for ~80 cycles (measured) against ~1 for FP32, so the step uses four FP64
+// instructions (b2, b3, a1 + w32, + correction) instead of ten.
+template <int M>
+__device__ __forceinline__ float newton_residual(float w, float B2, float L2, float B3, float L3,
+                                                 float S, float LS) {
+  // d = 1: (w - 0)^2 exactly
+  const float q = w * w, qe = fmaf(w, w, -q);
+  // d = 2: w - b2 = r2 + (er2 - L2)
+  float r2, er2;
+  two_sum(w, -B2, r2, er2);
+  const float e2 = er2 - L2;
+  const float p2 = r2 * r2, p2e = fmaf(r2, r2, -p2);
+  // s^2 = S^2 + 2 S LS + LS^2, S^2 exactly
+  const float ss = S * S, sse = fmaf(S, S, -ss);
+  float t1, c1, t2, c2;
+  two_sum(q, p2, t1, c1);
+  float small = c1 + qe + p2e - sse + fmaf(2.0f * r2, e2, e2 * e2) - fmaf(2.0f * S, LS, LS * LS);
+  if constexpr (M == 3) {
+    float r3, er3;
+    two_sum(w, -B3, r3, er3);
+    const float e3 = er3 - L3;
+    const float p3 = r3 * r3, p3e = fmaf(r3, r3, -p3);
+    float t0, c0;
+    two_sum(t1, p3, t0, c0);
+    t1 = t0;
+    small += c0 + p3e + fmaf(2.0f * r3, e3, e3 * e3);
+  }
+  two_sum(t1, -ss, t2, c2);
+  return t2 + (c2 + small);
+}
+
+// The correction delta solving f(w0) + f'(w0) delta + M delta^2 = 0 (f is a
+// quadratic with f'' = 2M) to second order: delta1 = -f / f', then
+// delta = delta1 (1 - M delta1 / f'), leaving an error O(delta1^3 / s^2).
+template <int M>
+__device__ __forceinline__ float newton_step(float f, float rinv) {
+  const float d1 = -f * rinv;
+  return d1 * fmaf(-(float)M * d1, rinv, 1.0f);
+}
+
 __device__ __forceinline__ double local_solve(double ax, double ay, double az, double s) {
   const double lo = dmin_nn(ax, ay), hi = dmax_nn(ax, ay);
   const double a1 = dmin_nn(lo, az), mid = dmax_nn(lo, az);
   const double a2 = dmin_nn(hi, mid), a3 = dmax_nn(hi, mid);
-  const double b2 = a2 - a1, b3 = a3 - a1, s2 = s * s;
+  const double b2 = a2 - a1, b3 = a3 - a1;
   // One term when a1 + s <= a2, tested as s <= b2 so that the sum stays off
   // the two- and three-term paths; a1 = +inf (no information) also returns
   // a1 + s = +inf.  Both tests run on the integer pipe.
   if (dle_nn(s, b2) || dbits(a1) >= dbits(CUDART_INF)) return a1 + s;
-  const float fs = f32_of_f64_nn(s), fb2 = f32_of_f64_nn(b2), fb3 = f32_of_f64_nn(b3);
-  const float fs2 = fs * fs;
-  const float w2 = 0.5f * (fb2 + sqrt_fast(fmaxf(2.0f * fs2 - fb2 * fb2, 0.0f)));
-  if (w2 <= fb3) {
-    const double w = f64_of_f32_nn(w2);
-    const double r2 = w - b2, t = fma(w, w, -s2), a1w = a1 + w;
-    const double f = fma(r2, r2, t);
-    const double rinv = f64_of_f32_nn(__fdividef(0.5f, 2.0f * w2 - fb2));
-    return fma(-f, rinv, a1w);
+  float S, LS, B2, L2, B3, L3;
+  split_nn(s, S, LS);
+  split_nn(b2, B2, L2);
+  split_nn(b3, B3, L3);  // b3 = +inf: B3 = +inf, L3 = 0
+  const float S2 = S * S;
+  const float w2 = 0.5f * (B2 + sqrt_fast(fmaxf(2.0f * S2 - B2 * B2, 0.0f)));
+  if (w2 <= B3) {
+    const double a1w = a1 + f64_of_f32_nn(w2);
+    const float f = newton_residual<2>(w2, B2, L2, 0.0f, 0.0f, S, LS);
+    return a1w + f64_of_f32(newton_step<2>(f, __fdividef(0.5f, 2.0f * w2 - B2)));
   }
-  const float e = fb3 - fb2;
-  const float d3 = 3.0f * fs2 - (fb2 * fb2 + fb3 * fb3 + e * e);
-  const float w3 = (fb2 + fb3 + sqrt_fast(fmaxf(d3, 0.0f))) * (1.0f / 3.0f);
-  const double w = f64_of_f32_nn(w3);
-  const double r2 = w - b2, r3 = w - b3, t = fma(w, w, -s2), a1w = a1 + w;
-  const double f = fma(r3, r3, fma(r2, r2, t));
-  const double rinv = f64_of_f32_nn(__fdividef(0.5f, 3.0f * w3 - fb2 - fb3));
-  return fma(-f, rinv, a1w);
+  const float e = B3 - B2;
+  const float d3 = 3.0f * S2 - (B2 * B2 + B3 * B3 + e * e);
+  const float w3 = (B2 + B3 + sqrt_fast(fmaxf(d3, 0.0f))) * (1.0f / 3.0f);
+  const double a1w = a1 + f64_of_f32_nn(w3);
+  const float f = newton_residual<3>(w3, B2, L2, B3, L3, S, LS);
+  return a1w + f64_of_f32(newton_step<3>(f, __fdividef(0.5f, 3.0f * w3 - B2 - B3)));
+}
+
+// Whether v - nv > kappa for stored values (>= 0), without an FP64
+// instruction: the drop in units of the last place of v (the bit-pattern
+// difference; exact within a binade, an over-count by at most 2x across
+// one, which only makes the test conservative) against kappa / ulp(v) in
+// FP32.  kf = kappa as a float.
+__device__ __forceinline__ bool drop_exceeds(double nv, double v, float kf) {
+  const long long iv = dbits(v), in = dbits(nv);
+  if (in >= iv) return false;
+  if (kf == 0.0f || iv >= dbits(CUDART_INF)) return true;
+  const unsigned long long D = (unsigned long long)(iv - in);
+  const int pe = 1075 - (int)(iv >> 52) + 127;  // 2^(1075 - e_v) = 1 / ulp(v), as a float
+  if (pe < 1 || pe > 254) return (v - nv) > (double)kf;
+  const float T = kf * __int_as_float(pe << 23);
+  const float Df = (D >> 32) ? __uint2float_rn((unsigned)(D >> 20)) * 1048576.0f
+                             : __uint2float_rn((unsigned)D);
+  return Df > T;
 }
 
 // Axis minimum of two neighbour values.

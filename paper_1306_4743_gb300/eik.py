@@ -33,7 +33,8 @@ PRECISIONS = {"fp64": 0, "fp32_polish": 1}
 EXPORTED = ("eik_opts_default", "eik_create", "eik_destroy", "eik_strerror",
             "eik_solve", "eik_solve_device", "eik_solve_batch",
             "eik_solve_batch_device", "eik_submit", "eik_poll", "eik_cancel",
-            "eik_solve_device_noalloc", "eik_autotune", "eik_struct_sizes")
+            "eik_solve_device_noalloc", "eik_autotune", "eik_struct_sizes",
+            "eik_selftest_local_solve", "eik_dfsm_solve_device")
 
 
 class Opts(ctypes.Structure):
@@ -126,6 +127,11 @@ def load(path: str | None = None):
     lib.eik_cancel.argtypes = [P, ctypes.c_uint64]
     lib.eik_solve_device_noalloc.argtypes = [P, D, P, P, P, D, P, P, ctypes.POINTER(Stats)]
     lib.eik_autotune.argtypes = [P, P, D, P, P, P, D, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.eik_selftest_local_solve.argtypes = [I, I64, ctypes.c_uint64, ctypes.POINTER(D),
+                                             ctypes.POINTER(D)]
+    lib.eik_dfsm_solve_device.argtypes = [P, D, P, P, P, D, I64, P, P,
+                                          ctypes.POINTER(I64), P, P,
+                                          ctypes.POINTER(Stats)]
     lib.eik_struct_sizes.argtypes = [ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]
     for name in EXPORTED:
@@ -140,6 +146,18 @@ def load(path: str | None = None):
     if path == LIB_PATH or _lib is None:
         _lib = lib
     return lib
+
+
+def selftest_local_solve(count=1 << 22, seed=1, device=0):
+    """Largest difference between the sweeps' FP64 local solve and the
+    direct FP64 closed forms over `count` random inputs: (in ulps of the
+    direct result, in units of ulp + 2^-44 s)."""
+    mu, mr = ctypes.c_double(), ctypes.c_double()
+    rc = load().eik_selftest_local_solve(int(device), int(count), int(seed), ctypes.byref(mu),
+                                         ctypes.byref(mr))
+    if rc != 0:
+        raise EikError(rc, "eik_selftest_local_solve")
+    return mu.value, mr.value
 
 
 def default_opts() -> Opts:
@@ -371,3 +389,34 @@ def solve(F, mask, q, h, tol=0.0, precision="fp32_polish", cell_n=0):
     with Solver(precision=precision, cell_n=cell_n) as s:
         u, _ = s.solve(F, mask, q, h, tol)
     return u
+
+
+def dfsm_solve(F, mask, q, h, tol=0.0, max_sweeps=4096, out=None, stream=None, check=True):
+    """Whole-grid sweeping baseline (eik_dfsm_solve_device) on torch CUDA
+    tensors F (float32), mask (uint8), q (float64), shape (nz, ny, nx).
+    Returns (u, stats_dict) with the per-sweep counts and largest decreases
+    in stats_dict["changed_per_sweep"] / ["max_drop_per_sweep"]."""
+    import torch
+    if not (_is_torch_cuda(F) and _is_torch_cuda(mask) and _is_torch_cuda(q)):
+        raise TypeError("dfsm_solve takes torch CUDA tensors")
+    F_t, m_t, q_t = F.contiguous(), mask.contiguous(), q.contiguous()
+    if F_t.dtype != torch.float32 or m_t.dtype != torch.uint8 or q_t.dtype != torch.float64:
+        raise TypeError("device inputs must be float32 F, uint8 mask, float64 q")
+    u = out if out is not None else torch.empty(F_t.shape, dtype=torch.float64, device=F_t.device)
+    s = stream if stream is not None else torch.cuda.current_stream(F_t.device).cuda_stream
+    nsw = ctypes.c_int64(0)
+    chg = (ctypes.c_int64 * int(max_sweeps))()
+    drop = (ctypes.c_double * int(max_sweeps))()
+    st = Stats()
+    with torch.cuda.device(F_t.device):
+        rc = load().eik_dfsm_solve_device(_dims_of(F_t.shape), float(h), F_t.data_ptr(),
+                                          m_t.data_ptr(), q_t.data_ptr(), float(tol),
+                                          int(max_sweeps), u.data_ptr(), ctypes.c_void_p(s),
+                                          ctypes.byref(nsw), chg, drop, ctypes.byref(st))
+    if rc != EIK_OK and check:
+        raise EikError(rc, "eik_dfsm_solve_device")
+    d = st.as_dict()
+    d["status"] = rc
+    d["changed_per_sweep"] = [int(chg[k]) for k in range(nsw.value)]
+    d["max_drop_per_sweep"] = [float(drop[k]) for k in range(nsw.value)]
+    return u, d

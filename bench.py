@@ -40,7 +40,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--edge", type=int, default=257)
     ap.add_argument("--cell-n", type=int, default=0)
-    ap.add_argument("--precision", default="fp32_polish", choices=["fp32_polish", "fp64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp32_polish", "fp64"],
+                    help="path of the headline single-instance solve (the other one is "
+                         "timed among the extras)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path and batch comparison lines")
@@ -77,14 +79,19 @@ def bytes_per_visit(n, es):
     return es * (n ** 3 + 6 * n * n) + es * n ** 3 + es * n ** 3 + 32
 
 
+# The sources that define the cell kernel: a traffic figure recorded in
+# profiles/ holds only while these are unchanged.
+CELL_KERNEL_SOURCES = ("eik_cells.cuh", "eik_cells_launch.cuh", "eik_cells_f32.cu",
+                       "eik_cells_f64.cu", "eik_device.cuh", "eik_internal.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1306_4743_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in CELL_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -198,7 +205,8 @@ def run_reference(args):
     }))
 
 
-def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, check=True):
+def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, check=True,
+                precision="fp32_polish", batch_nodes=None):
     """Poisson arrivals of solves (cubic edge log-uniform in [33, 385], speed
     fields from the Gaussian-bump family), continuous batching through
     eik_submit / eik_poll under an HBM budget.  Returns latency percentiles
@@ -207,8 +215,9 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
     import numpy as np
     draws = W.serving_requests(n=n_requests, rate=1.0, seed=5)
     uniq = [W.serving_problem(edge, seed) for (_, edge, seed) in draws[:n_unique]]
-    with eik.Solver(precision="fp32_polish", device=device,
-                    hbm_budget_bytes=int(budget_gb * (1 << 30))) as s:
+    with eik.Solver(precision=precision, device=device,
+                    hbm_budget_bytes=int(budget_gb * (1 << 30)),
+                    serve_batch_nodes=batch_nodes) as s:
         # closed loop: everything at once, to size the open-loop rate
         s.solve(uniq[0].F, uniq[0].mask, uniq[0].q, uniq[0].h, tol=tol)
         t0 = time.perf_counter()
@@ -253,7 +262,8 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
     return {"requests": n_requests, "unique_problems": n_unique,
             "rate_per_s": rate, "closed_loop_per_s": closed,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "nodes_per_s": nodes / span, "budget_gb": budget_gb,
+            "nodes_per_s": nodes / span, "budget_gb": budget_gb, "precision": precision,
+            "batch_nodes": batch_nodes,
             "edges": "cubic, round(exp(U[ln 33, ln 385])), seed 5; F: 8 Gaussian bumps, seed 5000+k"}
 
 
@@ -392,7 +402,20 @@ def run_ours(args):
         bt = [(torch.from_numpy(probs[k].F).to(dev), torch.from_numpy(probs[k].mask).to(dev),
                torch.from_numpy(probs[k].q).to(dev), probs[k].h) for k in mine]
         bnodes = sum(b.nodes for b in probs)
-        with eik.Solver(precision=args.precision, device=local) as sb:
+        # the FP64-path batch first, for comparison
+        with eik.Solver(precision="fp64", device=local) as sb:
+            outs, st = sb.solve_batch_device(bt, tol=args.tol)
+            ts = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                barrier()
+                outs, st = sb.solve_batch_device(bt, tol=args.tol, outs=outs)
+                ts.append(st["seconds"])
+        tb64 = max_over_ranks(statistics.mean(ts))
+        extras["batch256_fp64"] = {"nodes": bnodes, "nodes_per_s": bnodes / tb64,
+                                   "ms": tb64 * 1e3, "ranks": world}
+        # the FP32 + FP64-polish batch (one persistent launch per rank)
+        with eik.Solver(precision="fp32_polish", device=local) as sb:
             outs, st = sb.solve_batch_device(bt, tol=args.tol)
             ts = []
             for _ in range(3):
@@ -413,23 +436,28 @@ def run_ours(args):
                 errs.append(float(np.max(np.abs(o.cpu().numpy() - r)) / np.max(r)))
             batch_err = max(errs) if errs else None
         extras["batch256"] = {
+            "precision": "fp32_polish",
             "nodes": bnodes, "nodes_per_s": bnodes / tbatch,
             "ms": tbatch * 1e3, "cell_n": st["cell_n_used"], "ranks": world,
             "instances_rank0": len(mine),
             "max_rel_err_vs_oracle_sampled": batch_err}
         del bt, outs
     if rank == 0 and not args.no_extras:
-        # the plain single-instance FP64 path on the same grid (rank 0)
+        # the other precision mode, single instance, on the same grid (rank 0)
+        other = "fp32_polish" if args.precision == "fp64" else "fp64"
         u64 = torch.empty_like(u_d)
-        with eik.Solver(precision="fp64", cell_n=args.cell_n, device=local) as s64:
+        with eik.Solver(precision=other, cell_n=args.cell_n, device=local) as s64:
             s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
-            ts = []
-            for _ in range(3):
+            ts, tbo, tpo = [], [], []
+            for _ in range(5):
                 flush.fill_(1.0)
                 _, st = s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
                 ts.append(st["seconds"])
-        extras["fp64_single_instance"] = {
+                tbo.append(st["seconds_bulk"])
+                tpo.append(st["seconds_polish"])
+        extras[other + "_single_instance"] = {
             "nodes_per_s": p.nodes / statistics.mean(ts), "ms": statistics.mean(ts) * 1e3,
+            "bulk_ms": statistics.mean(tbo) * 1e3, "polish_ms": statistics.mean(tpo) * 1e3,
             "max_rel_err_vs_oracle": (float(np.max(np.abs(u64.cpu().numpy() - ref)) / np.max(ref))
                                       if cpu is not None else None)}
         # early termination (Sec. 6.4): error against the oracle and time per kappa
@@ -482,8 +510,11 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "node_updates_per_s": {
-            "fp32": statistics.mean(s["node_updates"] for s in stats) / tb if tb else None,
-            "fp64": statistics.mean(s["polish_node_updates"] for s in stats) / tp if tp else None},
+            ("bulk_fp32" if args.precision == "fp32_polish" else "bulk_fp64"):
+                statistics.mean(s["node_updates"] for s in stats) / tb if tb else None,
+            "polish_fp64": (statistics.mean(s["polish_node_updates"] for s in stats) / tp
+                            if tp else None)},
+        "fallback_used": int(sum(s["fallback_used"] for s in stats)),
         "visits": {"bulk": vb, "polish": vp, "cells": int(math.ceil(args.edge / n) ** 3)},
         "max_rel_err_vs_oracle": err_rel,
         # FP64 pipe view of the polish: ~14 FP64-pipe instructions per local

@@ -103,6 +103,12 @@ typedef struct {
                                (n + 1) h / 2 over the speed at the neighbour's
                                centre, with cell values kept (not reset to
                                +inf) when a cell is taken (Sec. 7) */
+  int reserved4;            /* must be 0 */
+  uint64_t serve_batch_nodes; /* serving: a batch takes waiting requests until
+                                 it holds this many grid nodes (at least one
+                                 request); 0 = default 64 M.  Smaller batches
+                                 start sooner, larger ones use the device
+                                 better. */
 } eik_opts;
 
 /* Counters and results of one solve (of the whole batch for batch calls). */
@@ -137,6 +143,10 @@ typedef struct {
   uint64_t revisits[2];         /* [bulk, polish]: visits of a cell that had
                                    converged before (restarted at its flagged faces) */
   uint64_t max_visit_sweeps[3]; /* [bulk, polish, fallback]: most sweeps in one visit */
+  double seconds_stage[3];      /* device time of the streaming stages: [init
+                                   (inputs to queued exit cells), FP32 -> FP64
+                                   hand-over and polish schedule, residual check +
+                                   fallback + copy-out] */
 } eik_stats;
 
 /* Default options. */

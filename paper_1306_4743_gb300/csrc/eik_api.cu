@@ -79,7 +79,7 @@ cudaError_t ensure_plane_table(eik_ctx* ctx, int n) {
     for (int c = 0; c < n; ++c)
       for (int b = 0; b < n; ++b) {
         const int a = C - b - c;
-        if (a >= 0 && a < n) tab.push_back((unsigned short)(a | (b << 5) | (c << 10)));
+        if (a >= 0 && a < n) tab.push_back((unsigned short)(a + n * (b + n * c)));
       }
   }
   off[np] = (int)tab.size();
@@ -113,7 +113,9 @@ struct LaunchPlan {
   long long max_rows = 0;  // largest ny * nz
   size_t off_key, off_state, off_dir, off_inst, off_next, off_deps, off_down, off_heads, off_ctl,
       off_nsrc;
-  size_t off_inst_b, off_inst64, off_tmap_b, off_tmap64, off_prep, off_pol, off_fin;
+  size_t off_inst_b, off_inst64, off_tmap_b, off_tmap64, off_prep, off_pol, off_fin, off_seg;
+  std::vector<int> seg;  // block schedule of the streaming kernels (host copy)
+  int seg_total[kNumSegKinds] = {0, 0, 0, 0, 0};
   size_t total = 0;
   size_t small_begin = 0, small_end = 0;  // tables copied from the host in one go
 };
@@ -210,7 +212,21 @@ void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, i
   L.off_prep = take(cur, (size_t)count * sizeof(PrepInstance));
   L.off_pol = take(cur, (size_t)count * sizeof(PolishInstance));
   L.off_fin = take(cur, (size_t)count * sizeof(FinalInstance));
+  L.off_seg = take(cur, segment_table_bytes(count));
   L.small_end = align_up(cur, 256);
+  {
+    std::vector<SegSizes> sz(count);
+    for (int t = 0; t < count; ++t) {
+      const InstPlan& I = L.inst[t];
+      sz[t].units[kSegPadB] = I.py * I.pz;
+      sz[t].units[kSegPad64] = I.py * I.pz;
+      sz[t].units[kSegRows] = (long long)I.ny * I.nz;
+      sz[t].units[kSegCellRows] = (long long)n * I.ncy * n * I.ncz;
+      sz[t].units[kSegCells] = I.ncells;
+    }
+    L.seg.assign(segment_table_bytes(count) / sizeof(int), 0);
+    make_segments(count, sz.data(), L.seg.data(), L.seg_total);
+  }
   L.total = L.small_end;
 }
 
@@ -440,6 +456,12 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     Fi.n = n;
   }
 
+  memcpy(hptr(L.off_seg), L.seg.data(), L.seg.size() * sizeof(int));
+  Segments segs;
+  segs.dev = reinterpret_cast<const int*>(A + L.off_seg);
+  segs.count = count;
+  for (int k = 0; k < kNumSegKinds; ++k) segs.total[k] = L.seg_total[k];
+
   // inputs and tables to the device
   if (host_io) {
     for (int t = 0; t < count; ++t) {
@@ -467,10 +489,9 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
 
   CK(cudaEventRecord(ex.ev[0], st));
   double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 0.25;
-  CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), count,
-                      L.max_padded_b, L.max_cellnodes, L.max_nodes, L.max_cells, L.total_cells,
+  CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), segs, L.total_cells,
                       cells, dctl, reinterpret_cast<int*>(A + L.off_nsrc), !polish, n, wf,
-                      ctx->opts.bulk_kappa_rel, ctx->sms, st));
+                      ctx->opts.bulk_kappa_rel, st));
 
   CellKernelParams p;
   p.inst = reinterpret_cast<const Instance*>(A + L.off_inst_b);
@@ -496,9 +517,8 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas));
   CK(cudaEventRecord(ex.ev[2], st));
   if (polish) {
-    CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), count,
-                          L.max_padded64, L.max_nodes, L.max_cells, L.total_cells, cells, dctl,
-                          ctx->sms, st));
+    CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), segs,
+                          L.total_cells, cells, dctl, st));
     p.inst = reinterpret_cast<const Instance*>(A + L.off_inst64);
     p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap64);
     p.pass = 1;
@@ -511,15 +531,14 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     // fallback, gated on the device: if some u ended below the fixed point
     // (lift too small), polish again with replace-mode sweeps
     CK(launch_fallback_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol),
-                            reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
-                            L.max_rows, L.max_cells, L.total_cells, cells, dctl, tol, ctx->sms,
-                            st));
+                            reinterpret_cast<const FinalInstance*>(A + L.off_fin), segs,
+                            L.total_cells, cells, dctl, tol, st));
     p.pass = 2;
     p.gated = 0;
     CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
   }
-  CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), count,
-                             L.max_rows, dctl, polish, tol, ctx->sms, st));
+  CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), segs, dctl,
+                             polish, tol, st));
   CK(cudaEventRecord(ex.ev[5], st));
   Control* hres = reinterpret_cast<Control*>(ex.h_ctl);
   CK(cudaMemcpyAsync(hres, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
@@ -553,9 +572,18 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
     stats->seconds = ms * 1e-3;
     cudaEventElapsedTime(&ms, ex.ev[1], ex.ev[2]);
     stats->seconds_bulk = ms * 1e-3;
+    cudaEventElapsedTime(&ms, ex.ev[0], ex.ev[1]);
+    stats->seconds_stage[0] = ms * 1e-3;
     if (polish) {
       cudaEventElapsedTime(&ms, ex.ev[3], ex.ev[4]);
       stats->seconds_polish = ms * 1e-3;
+      cudaEventElapsedTime(&ms, ex.ev[2], ex.ev[3]);
+      stats->seconds_stage[1] = ms * 1e-3;
+      cudaEventElapsedTime(&ms, ex.ev[4], ex.ev[5]);
+      stats->seconds_stage[2] = ms * 1e-3;
+    } else {
+      cudaEventElapsedTime(&ms, ex.ev[2], ex.ev[5]);
+      stats->seconds_stage[2] = ms * 1e-3;
     }
     stats->cell_visits = hres->counters[0][kCntVisits];
     stats->sweeps = hres->counters[0][kCntSweeps];
@@ -720,7 +748,7 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
   if (o.precision != EIK_FP64 && o.precision != EIK_FP32_POLISH) return EIK_EINVAL;
   if (o.cell_n != 0 && size_index(o.cell_n) < 0) return EIK_EINVAL;
   if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1 || o.cell_key < 0 ||
-      o.cell_key > 1)
+      o.cell_key > 1 || o.reserved4)
     return EIK_EINVAL;
   if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
   if (!(o.bulk_kappa_rel >= 0.0) || isinf(o.bulk_kappa_rel)) return EIK_EINVAL;
@@ -930,3 +958,6 @@ int eik_solve_batch_device(eik_ctx* ctx, int count, const int64_t* dims, const d
 
 eik::ServeState*& eik_serve_slot(eik_ctx* ctx) { return ctx->serve; }
 size_t eik_ctx_budget(eik_ctx* ctx) { return ctx->opts.hbm_budget_bytes; }
+unsigned long long eik_ctx_batch_nodes(eik_ctx* ctx) {
+  return ctx->opts.serve_batch_nodes ? ctx->opts.serve_batch_nodes : (64ull << 20);
+}

@@ -103,7 +103,7 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
   }
 }
 
-// Alg. 2 for one node (i, j, k) of the staged cell that is active: clear
+// Alg. 2 for one node si = i + n (j + n k) of the staged cell that is active: clear
 // its active bit, recompute it from its six neighbours (Eq. 2), store a
 // lower value (min mode) or any new value (replace mode), and on a change
 // by more than the threshold activate the neighbours that may now use it.
@@ -111,11 +111,11 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
 // the sweep has just left.
 template <typename T, int N, bool REPLACE>
 __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
-                                            unsigned* __restrict__ chg, int i, int j, int k,
-                                            int fx, int fy, int fz, T kappa,
-                                            unsigned& n_updates, unsigned& left) {
+                                            unsigned* __restrict__ chg, int si, int fx, int fy,
+                                            int fz, T kappa, unsigned& n_updates,
+                                            unsigned& left) {
   using G = Geo<T, N>;
-  const int si = i + N * (j + N * k);
+  const int i = si % N, j = (si / N) % N, k = si / (N * N);
   const T s = S[si];
   unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
   if (s < tinf<T>()) {
@@ -267,66 +267,69 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
   constexpr int UNR = (N >= 16 && WPC == 1) ? 6 : 2;
   static_assert(G::MAXPLANE <= UNR * NT, "a plane must fit one pass of the worker");
   static_assert(!COMPACT || WPC == 1, "the gathered list is per warp");
-  constexpr unsigned kNone = 0xffffu;  // packed entries use 15 bits
+  constexpr unsigned kNone = 0xffffu;  // node indices are below 4096
   const int fx = (dir & 1) ? N - 1 : 0;
   const int fy = (dir & 2) ? N - 1 : 0;
   const int fz = (dir & 4) ? N - 1 : 0;
-  // The plane table entries of the next plane are loaded while the current
-  // one is swept, so that after a plane's barrier only the active bits are
-  // still to be read.
-  unsigned nxt[UNR];
+  // n is a power of two, so the index of a node in the order of direction
+  // `dir` is the table's index with i, j, k reflected: one XOR
+  const unsigned dmask = (unsigned)(fx + N * (fy + N * fz));
+  // The table entries of the next two planes are loaded while the current
+  // plane is swept, so that after a plane's barrier only the active bits
+  // are still to be read.
+  unsigned nxt[UNR], nxt2[UNR];
   {
     const int b0 = off[first], e1 = off[first + 1];
+    const int b1 = first + 1 < G::NPLANES ? e1 : 0, e2 = first + 1 < G::NPLANES ? off[first + 2] : 0;
 #pragma unroll
     for (int h = 0; h < UNR; ++h) {
       const int e = b0 + tid + h * NT;
-      nxt[h] = e < e1 ? (unsigned)tab[e] : kNone;
+      nxt[h] = e < e1 ? ((unsigned)tab[e] ^ dmask) : kNone;
+      const int f = b1 + tid + h * NT;
+      nxt2[h] = f < e2 ? ((unsigned)tab[f] ^ dmask) : kNone;
     }
   }
   unsigned left = 0;
   for (int C = first; C < G::NPLANES; ++C) {
     unsigned cur[UNR];
 #pragma unroll
-    for (int h = 0; h < UNR; ++h) cur[h] = nxt[h];
-    if (C + 1 < G::NPLANES) {
-      const int b0 = off[C + 1], e1 = off[C + 2];
+    for (int h = 0; h < UNR; ++h) {
+      cur[h] = nxt[h];
+      nxt[h] = nxt2[h];
+    }
+    if (C + 2 < G::NPLANES) {
+      const int b0 = off[C + 2], e1 = off[C + 3];
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {
         const int e = b0 + tid + h * NT;
-        nxt[h] = e < e1 ? (unsigned)tab[e] : kNone;
+        nxt2[h] = e < e1 ? ((unsigned)tab[e] ^ dmask) : kNone;
       }
     }
+    // the active bits of all of this thread's nodes first (Alg. 2 l.1-2),
+    // so that their loads overlap
+    bool act[UNR];
+#pragma unroll
+    for (int h = 0; h < UNR; ++h)
+      act[h] = cur[h] != kNone && (chg[cur[h] & (unsigned)(G::N3 - 1)] & kActive);
     bool any;
     if constexpr (!COMPACT) {
       bool did = false;
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {
-        if (cur[h] == kNone) continue;
-        const int i = (int)(cur[h] & 31u) ^ fx;
-        const int j = (int)((cur[h] >> 5) & 31u) ^ fy;
-        const int k = (int)((cur[h] >> 10) & 31u) ^ fz;
-        if (!(chg[i + N * (j + N * k)] & kActive)) continue;  // Alg. 2 l.1-2
+        if (!act[h]) continue;
         did = true;
-        update_node<T, N, REPLACE>(U, S, chg, i, j, k, fx, fy, fz, kappa, n_updates, left);
+        update_node<T, N, REPLACE>(U, S, chg, (int)cur[h], fx, fy, fz, kappa, n_updates, left);
       }
       any = worker_any<WPC>(worker, did);  // also ends the plane
     } else {
-      // gather the plane's active nodes (as direction-applied i | j << 5 | k << 10)
+      // gather the plane's active nodes
       const int lane = tid & 31;
       const unsigned below = (1u << lane) - 1u;
       int total = 0;
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {
-        bool act = false;
-        unsigned pk = 0;
-        if (cur[h] != kNone) {
-          const int i = (int)(cur[h] & 31u) ^ fx, j = (int)((cur[h] >> 5) & 31u) ^ fy,
-                    k = (int)((cur[h] >> 10) & 31u) ^ fz;
-          act = (chg[i + N * (j + N * k)] & kActive) != 0;
-          pk = (unsigned)i | ((unsigned)j << 5) | ((unsigned)k << 10);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, act);
-        if (act) list[total + __popc(m & below)] = (unsigned short)pk;
+        const unsigned m = __ballot_sync(0xffffffffu, act[h]);
+        if (act[h]) list[total + __popc(m & below)] = (unsigned short)cur[h];
         total += __popc(m);
       }
       __syncwarp();
@@ -335,9 +338,7 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
         for (int h = 0; h < UNR; ++h) {
           const int x = x0 + h * NT;
           if (x >= total) break;
-          const unsigned pk = list[x];
-          update_node<T, N, REPLACE>(U, S, chg, (int)(pk & 31u), (int)((pk >> 5) & 31u),
-                                     (int)((pk >> 10) & 31u), fx, fy, fz, kappa, n_updates,
+          update_node<T, N, REPLACE>(U, S, chg, (int)list[x], fx, fy, fz, kappa, n_updates,
                                      left);
         }
       }
@@ -355,6 +356,9 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   using G = Geo<T, N>;
   constexpr int NT = WPC * 32;
   extern __shared__ __align__(128) unsigned char smem[];
+  // Nothing queued (the replace-mode fallback after a passing check, or all
+  // work already done): leave at once, as one block.
+  if (__syncthreads_and(ld_acquire_s32(&p.ctl->active) <= 0)) return;
   unsigned short* tab = reinterpret_cast<unsigned short*>(smem);
   int* off = reinterpret_cast<int*>(smem + G::TAB_BYTES);
   for (int e = threadIdx.x; e < G::N3; e += blockDim.x) tab[e] = p.plane_tab[e];

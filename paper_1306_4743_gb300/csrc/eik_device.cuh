@@ -203,7 +203,8 @@ __device__ __forceinline__ double dmax_nn(double a, double b) {
 }
 __device__ __forceinline__ bool dle_nn(double a, double b) { return dbits(a) <= dbits(b); }
 
-// Direct FP64 evaluation of the same root (used by the residual check).
+// Direct FP64 evaluation of the same root, with sqrt(double): the reference
+// eik_selftest_local_solve checks the sweeps' solve against.
 __device__ __forceinline__ double local_solve_direct(double ax, double ay, double az, double s) {
   const double lo = dmin_nn(ax, ay), hi = dmax_nn(ax, ay);
   const double a1 = dmin_nn(lo, az), mid = dmax_nn(lo, az);

@@ -110,7 +110,7 @@ struct CellKernelParams {
   const CUtensorMap* tmaps;      // one per instance, 64-byte aligned
   CellArrays cells;
   Control* ctl;
-  const unsigned short* plane_tab;  // packed (a | b << 5 | c << 10), by plane
+  const unsigned short* plane_tab;  // in-cell node index a + n (b + n c), by plane
   const int* plane_off;             // plane start offsets, 3(n-1)+2 entries
   unsigned long long spin_cap_ns;
   int max_sweeps;

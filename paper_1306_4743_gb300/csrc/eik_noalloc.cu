@@ -141,6 +141,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   const size_t off_tmap = take(cur, sizeof(CUtensorMap));
   const size_t off_prep = take(cur, sizeof(PrepInstance));
   const size_t off_fin = take(cur, sizeof(FinalInstance));
+  const size_t off_seg = take(cur, segment_table_bytes(1));
   const size_t off_tab = take(cur, (size_t)n3 * 2);
   const size_t off_off = take(cur, (size_t)(np + 1) * 4);
   const size_t small_end = up(cur, 256);
@@ -232,10 +233,23 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
       for (int c = 0; c < n; ++c)
         for (int b = 0; b < n; ++b) {
           const int a = C - b - c;
-          if (a >= 0 && a < n) tab[t++] = (unsigned short)(a | (b << 5) | (c << 10));
+          if (a >= 0 && a < n) tab[t++] = (unsigned short)(a + n * (b + n * c));
         }
     }
     off[np] = t;
+  }
+
+  Segments segs;
+  {
+    SegSizes sz;
+    sz.units[kSegPadB] = py * pz;
+    sz.units[kSegPad64] = py * pz;
+    sz.units[kSegRows] = (long long)ny * nz;
+    sz.units[kSegCellRows] = (long long)n * ncy * n * ncz;
+    sz.units[kSegCells] = ncells;
+    make_segments(1, &sz, reinterpret_cast<int*>(hp(off_seg)), segs.total);
+    segs.dev = reinterpret_cast<const int*>(A + off_seg);
+    segs.count = 1;
   }
 
   // Everything the solve reads before writing starts from these copies and
@@ -256,9 +270,8 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   cells.down = reinterpret_cast<unsigned*>(A + off_down);
   Control* dctl = reinterpret_cast<Control*>(A + off_ctl);
 
-  CKN(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + off_prep), 1, px * py * pz,
-                       ncells * n3, nodes, (int)ncells, (int)ncells, cells, dctl,
-                       reinterpret_cast<int*>(A + off_nsrc), true, n, 0.5, 0.0, slot->sms, st));
+  CKN(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + off_prep), segs, (int)ncells,
+                       cells, dctl, reinterpret_cast<int*>(A + off_nsrc), true, n, 0.5, 0.0, st));
   CellKernelParams p;
   memset(&p, 0, sizeof(p));
   p.inst = reinterpret_cast<const Instance*>(A + off_instance);
@@ -277,8 +290,8 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.cell_key = 0;
   int grid = 0;
   CKN(launch_cells(true, false, n, p, slot->sms, st, &grid));
-  CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), 1,
-                              (long long)ny * nz, dctl, false, 0.0, slot->sms, st));
+  CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), segs, dctl,
+                              false, 0.0, st));
   CKN(cudaMemcpyAsync(&g_host_ctl, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   CKN(cudaStreamSynchronize(st));
 

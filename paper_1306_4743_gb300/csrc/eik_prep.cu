@@ -9,17 +9,55 @@ namespace eik {
 
 namespace {
 
+// Block-wide reductions (every thread of the block calls them; the result
+// is valid in thread 0), so that a streaming kernel makes one atomic per
+// block on the shared control words instead of one per warp.
+template <typename V, typename Op>
+__device__ __forceinline__ V block_reduce(V v, Op op) {
+  __shared__ V part[32];
+  for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();  // part[] may still be read by a previous call
+  if ((threadIdx.x & 31) == 0) part[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 1; k < nw; ++k) v = op(v, part[k]);
+  return v;
+}
+struct MaxOp {
+  template <typename V> __device__ V operator()(V a, V b) const { return a > b ? a : b; }
+};
+struct MinOp {
+  template <typename V> __device__ V operator()(V a, V b) const { return a < b ? a : b; }
+};
+struct SumOp {
+  template <typename V> __device__ V operator()(V a, V b) const { return a + b; }
+};
+
 __device__ __forceinline__ void block_max_u64(unsigned long long v, unsigned long long* dst) {
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  if ((threadIdx.x & 31) == 0 && v) atomicMax(dst, v);
+  v = block_reduce(v, MaxOp());
+  if (threadIdx.x == 0 && v) atomicMax(dst, v);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// This block's instance and first unit (row or cell) under the block
+// schedule `seg` of one work kind: the last instance whose first block is
+// not after blockIdx.x.
+struct BlockWork {
+  int inst;
+  long long first;
+};
+__device__ __forceinline__ BlockWork block_work(const int* __restrict__ seg, int count, int per) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(seg + mid) <= b) lo = mid;
+    else hi = mid;
+  }
+  BlockWork w;
+  w.inst = lo;
+  w.first = (long long)(b - __ldg(seg + lo)) * per;
+  return w;
 }
 
 // Cell values of the cells that hold an exit node (Sec. 4: V^c = min q over
@@ -39,18 +77,17 @@ __device__ __forceinline__ void mark_exit_cells(const CellArrays& c, int cell_ba
   if (cc == N - 1 && cz + 1 < ncz) atomicMin(c.key + cell_base + lc + ncx * ncy, kq);
 }
 
-template <typename T>
-__global__ void reset_cells_kernel(const PrepInstance* __restrict__ pi, int count, CellArrays c) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
-  const PrepInstance P = pi[ii];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < P.ncells;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int g = P.cell_base + (int)e;
+__global__ void reset_cells_kernel(const PrepInstance* __restrict__ pi, const int* __restrict__ seg,
+                                   int count, CellArrays c) {
+  const BlockWork w = block_work(seg, count, kCellsPerBlock);
+  const PrepInstance P = pi[w.inst];
+  const long long lc = w.first + threadIdx.x;
+  if (threadIdx.x < kCellsPerBlock && lc < P.ncells) {
+    const int g = P.cell_base + (int)lc;
     c.key[g] = kKeyInf;
     c.state[g] = 0u;
     c.dir[g] = 0u;
-    c.inst[g] = ii;
+    c.inst[g] = w.inst;
     c.next[g] = 0u;
   }
 }
@@ -58,32 +95,32 @@ __global__ void reset_cells_kernel(const PrepInstance* __restrict__ pi, int coun
 // Smallest exit value over the launch, exit-node counts, q validation.  The
 // solver works on u - q_min internally (the system is shift invariant), so
 // every stored value is >= 0 and orders like its bit pattern.
-__global__ void minq_kernel(const PrepInstance* __restrict__ pi, int count, Control* ctl,
-                            int* n_src) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
-  const PrepInstance P = pi[ii];
-  const long long total = (long long)P.nx * P.ny * P.nz;
+__global__ void minq_kernel(const PrepInstance* __restrict__ pi, const int* __restrict__ seg,
+                            int count, Control* ctl, int* n_src) {
+  const BlockWork w = block_work(seg, count, kRowsPerBlock);
+  const PrepInstance P = pi[w.inst];
+  const long long rows = (long long)P.ny * P.nz;
   unsigned long long minq = ~0ull;
   int nsrc = 0, bad = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    if (P.mask[e]) {
-      const double qv = P.q[e];
-      if (!isfinite(qv)) bad = 1;
-      ++nsrc;
-      const unsigned long long o = ord_of_double(qv);
-      minq = o < minq ? o : minq;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long r = w.first + (threadIdx.x >> 5); r < w.first + kRowsPerBlock && r < rows;
+       r += nw) {
+    const long long base = r * P.nx;
+    for (int i = lane; i < P.nx; i += 32) {
+      if (P.mask[base + i]) {
+        const double qv = P.q[base + i];
+        if (!isfinite(qv)) bad = 1;
+        ++nsrc;
+        const unsigned long long o = ord_of_double(qv);
+        minq = o < minq ? o : minq;
+      }
     }
   }
-  for (int o = 16; o; o >>= 1) {
-    nsrc += __shfl_xor_sync(0xffffffffu, nsrc, o);
-    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    const unsigned long long w = __shfl_xor_sync(0xffffffffu, minq, o);
-    minq = w < minq ? w : minq;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (nsrc) atomicAdd(n_src + ii, nsrc);
+  nsrc = block_reduce(nsrc, SumOp());
+  bad = block_reduce(bad, MaxOp());
+  minq = block_reduce(minq, MinOp());
+  if (threadIdx.x == 0) {
+    if (nsrc) atomicAdd(n_src + w.inst, nsrc);
     if (bad) atomicExch(&ctl->bad_input, 1);
     if (minq != ~0ull) atomicMin(&ctl->min_q_ord, minq);
   }
@@ -96,75 +133,94 @@ __device__ __forceinline__ double q_base(const Control* ctl) {
 
 // Padded u: +inf everywhere except exit nodes, which hold q - q_min.
 template <typename T>
-__global__ void init_u_kernel(const PrepInstance* __restrict__ pi, int count, const Control* ctl) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
-  const PrepInstance P = pi[ii];
+__global__ void init_u_kernel(const PrepInstance* __restrict__ pi, const int* __restrict__ seg,
+                              int count, const Control* ctl) {
+  const BlockWork w = block_work(seg, count, kRowsPerBlock);
+  const PrepInstance P = pi[w.inst];
   const double qb = q_base(ctl);
   T* u = static_cast<T*>(P.u);
-  const long long total = P.px * P.py * P.pz;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long x = e % P.px, y = (e / P.px) % P.py, z = e / (P.px * P.py);
-    T v = tinf<T>();
-    if (x >= 1 && x <= P.nx && y >= 1 && y <= P.ny && z >= 1 && z <= P.nz) {
-      const long long lin = (x - 1) + P.nx * ((y - 1) + (long long)P.ny * (z - 1));
-      if (P.mask[lin]) v = (T)(P.q[lin] - qb);
+  const long long rows = P.py * P.pz;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long r = w.first + (threadIdx.x >> 5); r < w.first + kRowsPerBlock && r < rows;
+       r += nw) {
+    const int y = (int)(r % P.py), z = (int)(r / P.py);
+    const bool inside = y >= 1 && y <= P.ny && z >= 1 && z <= P.nz;
+    const long long lrow = inside ? (long long)P.nx * ((y - 1) + (long long)P.ny * (z - 1)) : 0;
+    T* urow = u + r * P.px;
+    for (int x = lane; x < P.px; x += 32) {
+      T v = tinf<T>();
+      if (inside && x >= 1 && x <= P.nx && P.mask[lrow + x - 1]) v = (T)(P.q[lrow + x - 1] - qb);
+      urow[x] = v;
     }
-    u[e] = v;
   }
 }
 
-// Cell-blocked slowness s = h / F (FP64 division, then rounded to T), +inf
+// s = h / F in FP64 from an FP32 reciprocal r and two FMA corrections
+// q <- q + r (h - q F): each multiplies the relative error by ~2^-24, so
+// from q0 = h r the result is within an ulp of the correctly rounded
+// quotient, with five FP64 instructions instead of a division.
+__device__ __forceinline__ double slowness(double h, float f) {
+  const double fd = (double)f;
+  const double r = (double)__frcp_rn(f);
+  const double q0 = h * r;
+  const double q1 = fma(fma(-q0, fd, h), r, q0);
+  return fma(fma(-q1, fd, h), r, q1);
+}
+
+// Cell-blocked slowness s = h / F (FP64, then rounded to T), +inf
 // at exit and filler nodes; cell values V^c = min q over exit nodes in the
 // cell (Sec. 4, initialisation of cell values), also given to cells that
 // hold a grid neighbour of an exit node; input validation.
 template <typename T>
-__global__ void init_s_kernel(const PrepInstance* __restrict__ pi, int count, CellArrays c,
-                              Control* ctl) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
-  const PrepInstance P = pi[ii];
-  const int N = P.n, N3 = N * N * N;
+__global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __restrict__ seg,
+                              int count, CellArrays c, Control* ctl) {
+  const BlockWork w = block_work(seg, count, kRowsPerBlock);
+  const PrepInstance P = pi[w.inst];
+  const int N = P.n, N3 = N * N * N, lg = __ffs(N) - 1, nm = N - 1;
   T* s = static_cast<T*>(P.s);
   double* s64 = static_cast<double*>(P.s64);
-  const long long total = (long long)P.ncells * N3;
+  const int ey = N * P.ncy, ex = N * P.ncx;  // extents covered by the cells
+  const long long rows = (long long)ey * N * P.ncz;
   const double qb = q_base(ctl);
   double acc = 0.0;
   unsigned long long cnt = 0;
   int bad = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int lc = (int)(e / N3), r = (int)(e % N3);
-    const int a = r % N, b = (r / N) % N, cc = r / (N * N);
-    const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
-    const long long i = (long long)N * cx + a, j = (long long)N * cy + b, k = (long long)N * cz + cc;
-    double sv = CUDART_INF;
-    if (i < P.nx && j < P.ny && k < P.nz) {
-      const long long lin = i + P.nx * (j + (long long)P.ny * k);
-      if (P.mask[lin]) {
-        mark_exit_cells(c, P.cell_base, P.ncx, P.ncy, P.ncz, N, lc, a, b, cc, cx, cy, cz,
-                        key_of((T)(P.q[lin] - qb)));
-      } else {
-        const float f = P.F[lin];
-        if (!(f > 0.0f) || isinf(f)) {
-          bad = 1;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long r = w.first + (threadIdx.x >> 5); r < w.first + kRowsPerBlock && r < rows;
+       r += nw) {
+    const int j = (int)(r % ey), k = (int)(r / ey);
+    const int b = j & nm, cc = k & nm, cy = j >> lg, cz = k >> lg;
+    const bool row_in = j < P.ny && k < P.nz;
+    const long long lrow = row_in ? (long long)P.nx * (j + (long long)P.ny * k) : 0;
+    for (int i = lane; i < ex; i += 32) {
+      const int a = i & nm, cx = i >> lg;
+      const int lc = cx + P.ncx * (cy + P.ncy * cz);
+      const long long e = (long long)lc * N3 + a + N * (b + N * cc);
+      double sv = CUDART_INF;  // filler nodes of partial edge cells stay fixed
+      if (row_in && i < P.nx) {
+        const long long lin = lrow + i;
+        if (P.mask[lin]) {
+          mark_exit_cells(c, P.cell_base, P.ncx, P.ncy, P.ncz, N, lc, a, b, cc, cx, cy, cz,
+                          key_of((T)(P.q[lin] - qb)));
         } else {
-          sv = P.h / (double)f;
-          acc += sv;
-          ++cnt;
+          const float f = P.F[lin];
+          if (!(f > 0.0f) || isinf(f)) {
+            bad = 1;
+          } else {
+            sv = slowness(P.h, f);
+            acc += sv;
+            ++cnt;
+          }
         }
       }
+      s[e] = (T)sv;
+      if (s64) s64[e] = sv;
     }
-    s[e] = (T)sv;
-    if (s64) s64[e] = sv;
   }
-  acc = warp_sum(acc);
-  for (int o = 16; o; o >>= 1) {
-    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
+  acc = block_reduce(acc, SumOp());
+  cnt = block_reduce(cnt, SumOp());
+  bad = block_reduce(bad, MaxOp());
+  if (threadIdx.x == 0) {
     if (cnt) {
       atomicAdd(&ctl->sum_s, acc);
       atomicAdd(&ctl->n_s, cnt);
@@ -216,38 +272,45 @@ __global__ void seed_sources_kernel(int total_cells, CellArrays c, Control* ctl,
 }
 
 // FP32 result -> FP64 padded array of the polish; largest finite value.
-__global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, int count, Control* ctl) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
-  const PolishInstance P = pi[ii];
+__global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, const int* __restrict__ seg,
+                                 int count, Control* ctl) {
+  const BlockWork w = block_work(seg, count, kRowsPerBlock);
+  const PolishInstance P = pi[w.inst];
   const double qb = q_base(ctl);
   const float* u32 = static_cast<const float*>(P.u32);
   double* u64 = static_cast<double*>(P.u64);
-  const long long total = P.px64 * P.py * P.pz;
+  const long long rows = P.py * P.pz;
   unsigned long long mx = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long x = e % P.px64, y = (e / P.px64) % P.py, z = e / (P.px64 * P.py);
-    double v = CUDART_INF;
-    if (x >= 1 && x <= P.nx && y >= 1 && y <= P.ny && z >= 1 && z <= P.nz) {
-      const long long lin = (x - 1) + P.nx * ((y - 1) + (long long)P.ny * (z - 1));
-      if (P.mask[lin]) {
-        v = P.q[lin] - qb;
-      } else {
-        // Lift the FP32 value above the FP64 fixed point: its rounding error
-        // grows at most ~2^-24 u per node along a characteristic (u is
-        // stored relative to q_min), so a lift of 2^-11 u covers paths of up
-        // to 2^13 nodes.  The monotone FP64 sweeps then descend to the fixed
-        // point.
-        v = (double)u32[x + P.px32 * (y + P.py * z)];
-        v += v * 4.8828125e-4;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long r = w.first + (threadIdx.x >> 5); r < w.first + kRowsPerBlock && r < rows;
+       r += nw) {
+    const int y = (int)(r % P.py), z = (int)(r / P.py);
+    const bool inside = y >= 1 && y <= P.ny && z >= 1 && z <= P.nz;
+    const long long lrow = inside ? (long long)P.nx * ((y - 1) + (long long)P.ny * (z - 1)) : 0;
+    const float* row32 = u32 + r * P.px32;
+    double* row64 = u64 + r * P.px64;
+    for (int x = lane; x < P.px64; x += 32) {
+      double v = CUDART_INF;
+      if (inside && x >= 1 && x <= P.nx) {
+        const long long lin = lrow + x - 1;
+        if (P.mask[lin]) {
+          v = P.q[lin] - qb;
+        } else {
+          // Lift the FP32 value above the FP64 fixed point: its rounding
+          // error grows at most ~2^-24 u per node along a characteristic (u
+          // is stored relative to q_min), so a lift of 2^-11 u covers paths
+          // of up to 2^13 nodes.  The monotone FP64 sweeps then descend to
+          // the fixed point.
+          v = (double)row32[x];
+          v += v * 4.8828125e-4;
+        }
+        if (isfinite(v)) {
+          const unsigned long long o = ord_of_double(v);
+          mx = o > mx ? o : mx;
+        }
       }
-      if (isfinite(v)) {
-        const unsigned long long o = ord_of_double(v);
-        mx = o > mx ? o : mx;
-      }
+      row64[x] = v;
     }
-    u64[e] = v;
   }
   block_max_u64(mx, &ctl->umax_bits);
 }
@@ -262,18 +325,19 @@ __device__ __forceinline__ bool fallback_needed(const Control* ctl, double kappa
   return check > 4.0 * kappa + 1e-13 * fmax(fabs(umax), 1.0);
 }
 
-__global__ void polish_keys_kernel(const PolishInstance* __restrict__ pi, int count,
-                                   CellArrays c, const Control* ctl, int gated, double kappa) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
+__global__ void polish_keys_kernel(const PolishInstance* __restrict__ pi,
+                                   const int* __restrict__ seg, int count, CellArrays c,
+                                   const Control* ctl, int gated, double kappa) {
   if (gated && (ctl->status || !fallback_needed(ctl, kappa))) return;
-  const PolishInstance P = pi[ii];
+  const BlockWork w = block_work(seg, count, kCellsPerBlock);
+  const PolishInstance P = pi[w.inst];
   const int N = P.n, N3 = N * N * N;
   const double* u64 = static_cast<const double*>(P.u64);
   const double* s64 = static_cast<const double*>(P.s64);
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int lc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; lc < P.ncells; lc += warps) {
+  const int warps = blockDim.x >> 5;
+  const long long end = w.first + kCellsPerBlock < P.ncells ? w.first + kCellsPerBlock : P.ncells;
+  for (int lc = (int)w.first + (threadIdx.x >> 5); lc < end; lc += warps) {
     const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
     double m = CUDART_INF;
     int at = 0;
@@ -316,18 +380,18 @@ __global__ void polish_keys_kernel(const PolishInstance* __restrict__ pi, int co
 // counts kept incoming edges, down[C] marks kept outgoing faces.  A cell is
 // queued once deps[C] reaches 0; an edge that was dropped is still honoured
 // by the flag protocol, which re-queues C if B's later values reach it.
-__global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi, int count,
-                                    CellArrays c) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
-  const PolishInstance P = pi[ii];
+__global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi,
+                                    const int* __restrict__ seg, int count, CellArrays c) {
+  const BlockWork w = block_work(seg, count, kCellsPerBlock);
+  const PolishInstance P = pi[w.inst];
   const int N = P.n, N3 = N * N * N;
   const double* u64 = static_cast<const double*>(P.u64);
   const double* s64 = static_cast<const double*>(P.s64);
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int warps = blockDim.x >> 5;
   const long long sy = P.px64, sz = P.px64 * P.py;
-  for (int lc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; lc < P.ncells; lc += warps) {
+  const long long end = w.first + kCellsPerBlock < P.ncells ? w.first + kCellsPerBlock : P.ncells;
+  for (int lc = (int)w.first + (threadIdx.x >> 5); lc < end; lc += warps) {
     const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
     const int g = P.cell_base + lc;
     const unsigned kc = c.key[g];
@@ -436,18 +500,20 @@ __global__ void seed_all_kernel(int total_cells, CellArrays c, Control* ctl, int
 
 // max |u - Lambda(u)| over non-exit grid nodes (FP64), count of non-finite
 // values, largest finite value, and the copy-out to the caller's layout.
+// Lambda is the sweeps' FP64 local solve (eik_selftest_local_solve pins it
+// to the direct FP64 closed forms): with `sqrt(double)` this pass was FP64-
+// pipe bound at ~1.6 ms per 257^3 grid.
 // MODE 0 (after the monotone polish) also records the residual as the
 // fallback check; MODE 1 is the final pass of the FP64 path; MODE 2 runs
 // only when the replace-mode fallback ran, and redoes MODE 0's final part.
-// Blocks take grid rows (fixed j, k) and threads the i of a row, so every
-// index is a shift or a 32-bit operation.
+// Blocks take grid rows (fixed j, k) and threads the i of a row.
 template <int MODE>
-__global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, int count,
-                                        Control* ctl, double kappa) {
-  const int ii = blockIdx.y;
-  if (ii >= count) return;
+__global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi,
+                                        const int* __restrict__ seg, int count, Control* ctl,
+                                        double kappa) {
   if (MODE == 2 && (ctl->status || !fallback_needed(ctl, kappa))) return;
-  const FinalInstance P = fi[ii];
+  const BlockWork w = block_work(seg, count, kRowsPerBlock);
+  const FinalInstance P = fi[w.inst];
   const double qb = q_base(ctl);
   const double* u = static_cast<const double*>(P.u64);
   const double* s = static_cast<const double*>(P.s64);
@@ -456,13 +522,15 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, in
   const long long sy = P.px64, sz = P.px64 * P.py;
   const int rows = P.ny * P.nz;
   unsigned long long rmax = 0, umax = 0, nbad = 0;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = (int)w.first + (threadIdx.x >> 5); row < w.first + kRowsPerBlock && row < rows;
+       row += nw) {
     const int j = row % P.ny, k = row / P.ny;
     const long long rbase = (long long)row * P.nx;
     const long long tbase = 1 + sy * (j + 1) + sz * (k + 1);
     const long long cbase = (long long)P.ncx * ((j >> lg) + (long long)P.ncy * (k >> lg));
     const int in_cell = ((j & nm) << lg) + ((k & nm) << (2 * lg));
-    for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
+    for (int i = lane; i < P.nx; i += 32) {
       const long long t = tbase + i;
       const double v = u[t];
       const long long e = rbase + i;
@@ -478,7 +546,7 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, in
       const double ax = nmin(u[t - 1], u[t + 1]);
       const double ay = nmin(u[t - sy], u[t + sy]);
       const double az = nmin(u[t - sz], u[t + sz]);
-      const double lam = local_solve_direct(ax, ay, az, sv);
+      const double lam = local_solve(ax, ay, az, sv);
       // A value left below the fixed point (lift too small) or above it (a
       // flag skipped on the FP32 error bound) both show here and send the
       // solve to the replace-mode fallback.
@@ -487,99 +555,106 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi, in
       rmax = rb > rmax ? rb : rmax;
     }
   }
-  if (MODE == 0) block_max_u64(rmax, &ctl->check_bits);
-  block_max_u64(rmax, &ctl->resid_bits);
-  block_max_u64(umax, &ctl->final_umax_bits);
-  for (int o = 16; o; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
-  if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(&ctl->nonfinite, nbad);
+  rmax = block_reduce(rmax, MaxOp());
+  umax = block_reduce(umax, MaxOp());
+  nbad = block_reduce(nbad, SumOp());
+  if (threadIdx.x == 0) {
+    if (MODE == 0 && rmax) atomicMax(&ctl->check_bits, rmax);
+    if (rmax) atomicMax(&ctl->resid_bits, rmax);
+    if (umax) atomicMax(&ctl->final_umax_bits, umax);
+    if (nbad) atomicAdd(&ctl->nonfinite, nbad);
+  }
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Host launchers.
-static dim3 stream_grid(long long work, int count, int sms) {
-  long long blocks = (work + 255) / 256;
-  const long long cap = (long long)sms * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  return dim3((unsigned)blocks, (unsigned)count, 1);
+// Host side: block schedule and launchers.
+size_t segment_table_bytes(int count) {
+  return (size_t)kNumSegKinds * (size_t)(count + 1) * sizeof(int);
 }
 
-cudaError_t launch_bulk_init(const PrepInstance* d_pi, int count, long long max_padded,
-                             long long max_cellnodes, long long max_nodes, int max_cells,
-                             int total_cells, CellArrays cells, Control* ctl, int* n_src, bool fp64,
-                             int n, double width_factor, double kappa_rel, int sms,
-                             cudaStream_t st) {
-  reset_cells_kernel<float><<<stream_grid(max_cells, count, sms), 256, 0, st>>>(d_pi, count, cells);
-  minq_kernel<<<stream_grid(max_nodes, count, sms), 256, 0, st>>>(d_pi, count, ctl, n_src);
-  if (fp64) {
-    init_u_kernel<double><<<stream_grid(max_padded, count, sms), 256, 0, st>>>(d_pi, count, ctl);
-    init_s_kernel<double>
-        <<<stream_grid(max_cellnodes, count, sms), 256, 0, st>>>(d_pi, count, cells, ctl);
-  } else {
-    init_u_kernel<float><<<stream_grid(max_padded, count, sms), 256, 0, st>>>(d_pi, count, ctl);
-    init_s_kernel<float>
-        <<<stream_grid(max_cellnodes, count, sms), 256, 0, st>>>(d_pi, count, cells, ctl);
+void make_segments(int count, const SegSizes* sizes, int* host_seg, int* totals) {
+  const long long per[kNumSegKinds] = {kRowsPerBlock, kRowsPerBlock, kRowsPerBlock,
+                                       kRowsPerBlock, kCellsPerBlock};
+  for (int k = 0; k < kNumSegKinds; ++k) {
+    int* t = host_seg + (size_t)k * (count + 1);
+    long long acc = 0;
+    for (int i = 0; i < count; ++i) {
+      t[i] = (int)acc;
+      const long long u = sizes[i].units[k];
+      acc += (u + per[k] - 1) / per[k];
+    }
+    t[count] = (int)acc;
+    totals[k] = (int)acc;
   }
-  setup_bulk_kernel<<<1, 32, 0, st>>>(ctl, n_src, count, n, width_factor, kappa_rel);
+}
+
+static inline const int* seg_of(const Segments& g, int kind) {
+  return g.dev + (size_t)kind * (g.count + 1);
+}
+static inline unsigned blocks_of(const Segments& g, int kind) {
+  return (unsigned)(g.total[kind] > 0 ? g.total[kind] : 1);
+}
+
+cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& g, int total_cells,
+                             CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
+                             double width_factor, double kappa_rel, cudaStream_t st) {
+  const int c = g.count;
+  reset_cells_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells);
+  minq_kernel<<<blocks_of(g, kSegRows), 256, 0, st>>>(d_pi, seg_of(g, kSegRows), c, ctl, n_src);
+  if (fp64) {
+    init_u_kernel<double><<<blocks_of(g, kSegPadB), 256, 0, st>>>(d_pi, seg_of(g, kSegPadB), c, ctl);
+    init_s_kernel<double><<<blocks_of(g, kSegCellRows), 256, 0, st>>>(
+        d_pi, seg_of(g, kSegCellRows), c, cells, ctl);
+  } else {
+    init_u_kernel<float><<<blocks_of(g, kSegPadB), 256, 0, st>>>(d_pi, seg_of(g, kSegPadB), c, ctl);
+    init_s_kernel<float><<<blocks_of(g, kSegCellRows), 256, 0, st>>>(
+        d_pi, seg_of(g, kSegCellRows), c, cells, ctl);
+  }
+  setup_bulk_kernel<<<1, 32, 0, st>>>(ctl, n_src, c, n, width_factor, kappa_rel);
   seed_sources_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells,
                                                                             ctl, 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_polish_prep(const PolishInstance* d_pi, int count, long long max_padded64,
-                               long long max_nodes, int max_cells, int total_cells,
-                               CellArrays cells, Control* ctl, int sms, cudaStream_t st) {
-  convert_u_kernel<<<stream_grid(max_padded64, count, sms), 256, 0, st>>>(d_pi, count, ctl);
-  long long blocks = ((long long)max_cells * 32 + 255) / 256;
-  if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
-  if (blocks < 1) blocks = 1;
-  polish_keys_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count, cells,
-                                                                            ctl, 0, 0.0);
-  polish_graph_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count, cells);
+cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& g, int total_cells,
+                               CellArrays cells, Control* ctl, cudaStream_t st) {
+  const int c = g.count;
+  convert_u_kernel<<<blocks_of(g, kSegPad64), 256, 0, st>>>(d_pi, seg_of(g, kSegPad64), c, ctl);
+  polish_keys_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells,
+                                                              ctl, 0, 0.0);
+  polish_graph_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c,
+                                                               cells);
   setup_polish_kernel<<<1, 32, 0, st>>>(ctl, 0, 0.0);
   seed_ready_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells,
                                                                           ctl);
   return cudaGetLastError();
 }
 
-static dim3 row_grid(long long rows, int count, int sms) {
-  long long blocks = rows;
-  const long long cap = (long long)sms * 16;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  return dim3((unsigned)blocks, (unsigned)count, 1);
-}
-
-cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi, int count,
-                                 long long max_rows, int max_cells, int total_cells,
-                                 CellArrays cells, Control* ctl, double kappa, int sms,
-                                 cudaStream_t st) {
-  residual_extract_kernel<0><<<row_grid(max_rows, count, sms), 128, 0, st>>>(d_fi, count, ctl,
-                                                                             kappa);
-  {
-    long long blocks = ((long long)max_cells * 32 + 255) / 256;
-    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
-    if (blocks < 1) blocks = 1;
-    polish_keys_kernel<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(d_pi, count, cells,
-                                                                              ctl, 1, kappa);
-  }
+cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi,
+                                 const Segments& g, int total_cells, CellArrays cells,
+                                 Control* ctl, double kappa, cudaStream_t st) {
+  const int c = g.count;
+  residual_extract_kernel<0><<<blocks_of(g, kSegRows), 256, 0, st>>>(d_fi, seg_of(g, kSegRows), c,
+                                                                     ctl, kappa);
+  polish_keys_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells,
+                                                              ctl, 1, kappa);
   setup_polish_kernel<<<1, 32, 0, st>>>(ctl, 1, kappa);
   seed_all_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells, ctl,
                                                                         2, 1, kappa);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_rows,
-                                    Control* ctl, bool after_fallback, double kappa, int sms,
-                                    cudaStream_t st) {
+cudaError_t launch_residual_extract(const FinalInstance* d_fi, const Segments& g, Control* ctl,
+                                    bool after_fallback, double kappa, cudaStream_t st) {
+  const int c = g.count;
   if (after_fallback)
-    residual_extract_kernel<2><<<row_grid(max_rows, count, sms), 128, 0, st>>>(d_fi, count, ctl,
-                                                                               kappa);
+    residual_extract_kernel<2><<<blocks_of(g, kSegRows), 256, 0, st>>>(d_fi, seg_of(g, kSegRows),
+                                                                       c, ctl, kappa);
   else
-    residual_extract_kernel<1><<<row_grid(max_rows, count, sms), 128, 0, st>>>(d_fi, count, ctl,
-                                                                               kappa);
+    residual_extract_kernel<1><<<blocks_of(g, kSegRows), 256, 0, st>>>(d_fi, seg_of(g, kSegRows),
+                                                                       c, ctl, kappa);
   return cudaGetLastError();
 }
 

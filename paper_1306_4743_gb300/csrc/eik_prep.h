@@ -48,24 +48,51 @@ struct FinalInstance {
   int n;
 };
 
-cudaError_t launch_bulk_init(const PrepInstance* d_pi, int count, long long max_padded,
-                             long long max_cellnodes, long long max_nodes, int max_cells,
-                             int total_cells, CellArrays cells, Control* ctl, int* n_src, bool fp64,
-                             int n, double width_factor, double kappa_rel, int sms,
-                             cudaStream_t st);
-cudaError_t launch_polish_prep(const PolishInstance* d_pi, int count, long long max_padded64,
-                               long long max_nodes, int max_cells, int total_cells,
-                               CellArrays cells, Control* ctl, int sms, cudaStream_t st);
-cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi, int count,
-                                 long long max_rows, int max_cells, int total_cells,
-                                 CellArrays cells, Control* ctl, double kappa, int sms,
-                                 cudaStream_t st);
-// max_rows: the largest ny * nz of the launch.  after_fallback: the pass
-// after the replace-mode fallback (a no-op on the device unless it ran);
-// otherwise the final pass of the FP64 path.
-cudaError_t launch_residual_extract(const FinalInstance* d_fi, int count, long long max_rows,
-                                    Control* ctl, bool after_fallback, double kappa, int sms,
-                                    cudaStream_t st);
+// Block schedule of the streaming kernels.  Their blocks are spread over the
+// instances of a launch in proportion to each instance's work, so a batch of
+// uneven grids launches no idle blocks and no block needs a division of a
+// 64-bit index: a block takes kRowsPerBlock rows (fixed j, k) of one
+// instance, one warp per row with its lanes striding over i (rows of small
+// grids are short), or kCellsPerBlock cells.
+//   rows of the padded bulk array   py * pz       (row length px of the pass)
+//   rows of the padded FP64 array   py * pz       (px64)
+//   grid rows                       ny * nz       (nx)
+//   rows of the cell-blocked array  (n ncy) * (n ncz)   (n ncx)
+//   cells                           ncells
+enum SegKind { kSegPadB = 0, kSegPad64, kSegRows, kSegCellRows, kSegCells, kNumSegKinds };
+constexpr int kRowsPerBlock = 32;
+constexpr int kCellsPerBlock = 16;  // 8 warps, 2 cells each
+
+// Work of one instance in the units above.
+struct SegSizes {
+  long long units[kNumSegKinds];
+};
+
+// seg table on the device: (count + 1) ints per kind, seg[k (count + 1) + t]
+// = first block of instance t, ... + count = total blocks of kind k; the
+// host keeps the totals for the launch sizes.
+struct Segments {
+  const int* dev;
+  int count;
+  int total[kNumSegKinds];
+};
+
+// Fills host_seg ((count + 1) * kNumSegKinds ints) and totals.
+void make_segments(int count, const SegSizes* sizes, int* host_seg, int* totals);
+size_t segment_table_bytes(int count);
+
+cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& seg, int total_cells,
+                             CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
+                             double width_factor, double kappa_rel, cudaStream_t st);
+cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& seg, int total_cells,
+                               CellArrays cells, Control* ctl, cudaStream_t st);
+cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi,
+                                 const Segments& seg, int total_cells, CellArrays cells,
+                                 Control* ctl, double kappa, cudaStream_t st);
+// after_fallback: the pass after the replace-mode fallback (a no-op on the
+// device unless it ran); otherwise the final pass of the FP64 path.
+cudaError_t launch_residual_extract(const FinalInstance* d_fi, const Segments& seg, Control* ctl,
+                                    bool after_fallback, double kappa, cudaStream_t st);
 
 // Persistent cell kernels (eik_cells_f32.cu / eik_cells_f64.cu).
 cudaError_t launch_cells(bool fp64, bool replace, int n, const CellKernelParams& p, int sms,

@@ -2,8 +2,8 @@
 // continuous batching over a few execution slots.
 //
 // A submitted request waits in arrival order.  Whenever a slot is free, the
-// waiting requests at the front (same tolerance, up to kMaxBatch) are
-// launched together as one batch -- one persistent cell kernel over all
+// waiting requests at the front (same tolerance, up to kMaxBatch requests
+// and opts.serve_batch_nodes grid nodes) are launched together as one batch -- one persistent cell kernel over all
 // their cells -- on that slot's own stream, as long as the device memory of
 // all busy slots plus the new batch fits the context's budget.  Batches on
 // different slots run concurrently on the device, so requests that arrive
@@ -144,8 +144,11 @@ void admit(eik_ctx* ctx, ServeState* s) {
     std::vector<int64_t> dims;
     std::vector<double> hs;
     const double tol = s->req[s->waiting.front()]->tol;
+    const unsigned long long cap_nodes = eik_ctx_batch_nodes(ctx);
+    unsigned long long batch_nodes = 0;
     size_t bytes = 0;
-    for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)ids.size() < kMaxBatch;
+    for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)ids.size() < kMaxBatch &&
+                                           (ids.empty() || batch_nodes < cap_nodes);
          ++it) {
       Request* r = s->req[*it];
       if (r->tol != tol) continue;
@@ -160,6 +163,7 @@ void admit(eik_ctx* ctx, ServeState* s) {
       }
       bytes = b;
       ids.push_back(*it);
+      batch_nodes += (unsigned long long)(r->dims[0] * r->dims[1] * r->dims[2]);
     }
     if (ids.empty()) {
       const uint64_t id = s->waiting.front();

@@ -57,6 +57,7 @@ void serve_destroy(ServeState* s);
 size_t eik_plan_bytes(eik_ctx* ctx, int count, const int64_t* dims, const double* h,
                       bool host_io);
 size_t eik_ctx_budget(eik_ctx* ctx);
+unsigned long long eik_ctx_batch_nodes(eik_ctx* ctx);
 
 // Enqueue a batch on `ex` / `st`.  With async_out, host outputs are staged in
 // pinned memory and copied to the caller's buffers by eik_finish_batch.

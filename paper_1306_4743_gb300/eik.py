@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
                 ("max_sweeps_per_visit", ctypes.c_int),
                 ("queue_order", ctypes.c_int),
                 ("bulk_kappa_rel", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("cell_key", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("cell_key", ctypes.c_int),
+                ("reserved4", ctypes.c_int), ("serve_batch_nodes", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
@@ -69,7 +70,8 @@ class Stats(ctypes.Structure):
                 ("fallback_visits", ctypes.c_uint64),
                 ("phase_seconds", (ctypes.c_double * 4) * 2),
                 ("revisits", ctypes.c_uint64 * 2),
-                ("max_visit_sweeps", ctypes.c_uint64 * 3)]
+                ("max_visit_sweeps", ctypes.c_uint64 * 3),
+                ("seconds_stage", ctypes.c_double * 3)]
 
     def as_dict(self):
         d = {}
@@ -79,6 +81,8 @@ class Stats(ctypes.Structure):
                 v = [[v[i][j] for j in range(4)] for i in range(2)]
             elif name in ("revisits", "max_visit_sweeps"):
                 v = [int(x) for x in v]
+            elif name == "seconds_stage":
+                v = [float(x) for x in v]
             d[name] = v
         return d
 
@@ -169,7 +173,7 @@ def default_opts() -> Opts:
 def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
               spin_cap_us=None, bucket_width=None, max_sweeps_per_visit=None, max_ctas=0,
               bulk_kappa_rel=None, queue_order=None, use_graphs=None,
-              cell_key=None) -> Opts:
+              cell_key=None, serve_batch_nodes=None) -> Opts:
     """eik_opts from the library defaults with the given fields changed
     (None = keep the default)."""
     o = default_opts()
@@ -192,6 +196,8 @@ def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
         o.use_graphs = int(use_graphs)
     if cell_key is not None:
         o.cell_key = int(cell_key)
+    if serve_batch_nodes is not None:
+        o.serve_batch_nodes = int(serve_batch_nodes)
     return o
 
 
@@ -221,14 +227,15 @@ class Solver:
     def __init__(self, precision="fp32_polish", cell_n=0, device=0,
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
                  max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
-                 queue_order=None, use_graphs=None, cell_key=None):
+                 queue_order=None, use_graphs=None, cell_key=None, serve_batch_nodes=None):
         """Options left at None keep the library defaults (eik_opts_default)."""
         self.lib = load()
         o = make_opts(precision=precision, cell_n=cell_n, device=device,
                       hbm_budget_bytes=hbm_budget_bytes, spin_cap_us=spin_cap_us,
                       bucket_width=bucket_width, max_sweeps_per_visit=max_sweeps_per_visit,
                       max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
-                      queue_order=queue_order, use_graphs=use_graphs, cell_key=cell_key)
+                      queue_order=queue_order, use_graphs=use_graphs, cell_key=cell_key,
+                      serve_batch_nodes=serve_batch_nodes)
         self.opts = o
         self._outputs = {}  # ticket -> output array, alive until done or cancelled
         self.ctx = ctypes.c_void_p()

@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path and batch comparison lines")
-    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--serve-unique", type=int, default=24)
     ap.add_argument("--tol", type=float, default=1e-12,
                     help="kappa of the FP64 sweeps (early-termination threshold)")
@@ -218,19 +218,22 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
     with eik.Solver(precision=precision, device=device,
                     hbm_budget_bytes=int(budget_gb * (1 << 30)),
                     serve_batch_nodes=batch_nodes) as s:
-        # closed loop: everything at once, to size the open-loop rate
+        # closed loop: everything at once, to size the open-loop rate; the
+        # first round only warms the execution slots (device arenas, pinned
+        # staging), the second is timed
         s.solve(uniq[0].F, uniq[0].mask, uniq[0].q, uniq[0].h, tol=tol)
-        t0 = time.perf_counter()
-        tickets = [s.submit(p.F, p.mask, p.q, p.h, tol=tol)[0] for p in uniq]
-        left = set(tickets)
-        while left:
-            for t in list(left):
-                if s.poll(t)[0]:
-                    left.discard(t)
-        closed = len(uniq) / (time.perf_counter() - t0)
+        for rnd in range(2):
+            t0 = time.perf_counter()
+            tickets = [s.submit(p.F, p.mask, p.q, p.h, tol=tol)[0] for p in uniq]
+            left = set(tickets)
+            while left:
+                for t in list(left):
+                    if s.poll(t)[0]:
+                        left.discard(t)
+            closed = len(uniq) / (time.perf_counter() - t0)
         rate = 0.7 * closed
         arrivals = [a for (a, _, _) in W.serving_requests(n=n_requests, rate=rate, seed=5)]
-        lat, nodes, out = [], 0, {}
+        lat, nodes, out, kept = [], 0, {}, {}
         nxt = 0
         t0 = time.perf_counter()
         while len(lat) < n_requests:
@@ -249,21 +252,24 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
                     lat.append(time.perf_counter() - t0 - arr)
                     nodes += uniq[k % n_unique].nodes
                     if check and k < n_unique and uniq[k].nodes <= 129 ** 3 and k % 3 == 0:
-                        import oracle
-                        pr = uniq[k]
-                        ref = oracle.fmm(pr.F, pr.mask, pr.q, pr.h)
-                        e = float(np.max(np.abs(u - ref)) / np.max(ref))
-                        if e > 1e-9:
-                            raise RuntimeError("serving request %d error %.2e" % (k, e))
+                        kept[k] = u  # checked against the oracle after the timed loop
             if not out and nxt < n_requests:
                 time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.002)))
         span = time.perf_counter() - t0
+    if kept:
+        import oracle
+        for k, u in kept.items():
+            pr = uniq[k]
+            ref = oracle.fmm(pr.F, pr.mask, pr.q, pr.h)
+            e = float(np.max(np.abs(u - ref)) / np.max(ref))
+            if e > 1e-9:
+                raise RuntimeError("serving request %d error %.2e" % (k, e))
     lat_ms = np.sort(np.array(lat)) * 1e3
     return {"requests": n_requests, "unique_problems": n_unique,
             "rate_per_s": rate, "closed_loop_per_s": closed,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "nodes_per_s": nodes / span, "budget_gb": budget_gb, "precision": precision,
-            "batch_nodes": batch_nodes,
+            "batch_nodes": batch_nodes, "checked_vs_oracle": len(kept),
             "edges": "cubic, round(exp(U[ln 33, ln 385])), seed 5; F: 8 Gaussian bumps, seed 5000+k"}
 
 
@@ -491,6 +497,9 @@ def run_ours(args):
         extras["serving"] = run_serving(eik, W, local, args.serve_requests,
                                         args.serve_unique, tol=args.tol,
                                         check=cpu is not None)
+        extras["serving_fp64"] = run_serving(eik, W, local, args.serve_requests,
+                                             args.serve_unique, tol=args.tol, check=False,
+                                             precision="fp64")
 
     out = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,

@@ -263,8 +263,9 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
   using G = Geo<T, N>;
   constexpr int NT = WPC * 32;
   // Nodes of one plane do not depend on each other: a thread takes up to UNR
-  // of them, so their loads and arithmetic overlap; every plane fits.
-  constexpr int UNR = (N >= 16 && WPC == 1) ? 6 : 2;
+  // of them (so their loads and arithmetic overlap) and every plane fits one
+  // pass of the worker.
+  constexpr int UNR = (G::MAXPLANE + NT - 1) / NT;
   static_assert(G::MAXPLANE <= UNR * NT, "a plane must fit one pass of the worker");
   static_assert(!COMPACT || WPC == 1, "the gathered list is per warp");
   constexpr unsigned kNone = 0xffffu;  // node indices are below 4096

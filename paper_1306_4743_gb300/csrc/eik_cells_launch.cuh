@@ -1,8 +1,9 @@
 // eik_cells_launch.cuh -- launch configuration of the persistent cell kernel
-// per (value type, cell size): a worker is one warp for n <= 8 and four warps
-// for n = 16 (the sweep of one cell is on the critical path, so a 16^3 cell
-// gets more lanes per plane); grid = SM count x resident CTAs per SM, at
-// most two per SM by default.
+// per (value type, cell size): a worker is one warp for n <= 8 and six warps
+// for n = 16, one thread per node of the largest plane (192 nodes), so a
+// plane step is one node deep (measured: 4 warps 20.6 ms, 6 warps 18.8 ms,
+// 8 warps 18.9 ms on the 257^3 FP64 solve); grid = SM count x resident CTAs
+// per SM, at most two per SM by default.
 #pragma once
 #include "eik_cells.cuh"
 #include "eik_prep.h"
@@ -16,7 +17,7 @@ struct WorkerShape<4> { static constexpr int WPC = 1, WORKERS = 8; };
 template <>
 struct WorkerShape<8> { static constexpr int WPC = 1, WORKERS = 4; };
 template <>
-struct WorkerShape<16> { static constexpr int WPC = 4, WORKERS = 1; };
+struct WorkerShape<16> { static constexpr int WPC = 6, WORKERS = 1; };
 
 template <typename T, int N>
 constexpr int cells_smem_bytes() {

@@ -142,6 +142,8 @@ typedef struct {
                                    summed over workers */
   uint64_t revisits[2];         /* [bulk, polish]: visits of a cell that had
                                    converged before (restarted at its flagged faces) */
+  uint64_t revisit_sweeps[2];   /* ... the sweeps of those visits */
+  uint64_t revisit_updates[2];  /* ... and their node updates */
   uint64_t max_visit_sweeps[3]; /* [bulk, polish, fallback]: most sweeps in one visit */
   double seconds_stage[3];      /* device time of the streaming stages: [init
                                    (inputs to queued exit cells), FP32 -> FP64

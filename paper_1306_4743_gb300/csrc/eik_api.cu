@@ -111,6 +111,7 @@ struct LaunchPlan {
   int total_cells = 0, max_cells = 0;
   long long max_padded_b = 0, max_padded64 = 0, max_cellnodes = 0, max_nodes = 0;
   long long max_rows = 0;  // largest ny * nz
+  size_t off_lev_perm = 0, off_lev_off = 0, off_lev_depth = 0;  // polish only
   size_t off_key, off_state, off_dir, off_inst, off_next, off_deps, off_down, off_heads, off_ctl,
       off_nsrc;
   size_t off_inst_b, off_inst64, off_tmap_b, off_tmap64, off_prep, off_pol, off_fin, off_seg;
@@ -200,6 +201,11 @@ void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, i
   L.off_next = take(cur, (size_t)cells * 4);
   L.off_deps = take(cur, (size_t)cells * 4);
   L.off_down = take(cur, (size_t)cells * 4);
+  if (polish) {
+    L.off_lev_perm = take(cur, (size_t)cells * n * n * n * 2);
+    L.off_lev_off = take(cur, (size_t)cells * (kMaxLevels + 1) * 2);
+    L.off_lev_depth = take(cur, (size_t)cells * 4);
+  }
   L.off_heads = take(cur, (size_t)kNumBuckets * 12);  // heads, then run counts
   // small tables, filled on the host and copied in one transfer
   L.small_begin = align_up(cur, 256);
@@ -485,6 +491,9 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   cells.run = reinterpret_cast<int*>(A + L.off_heads + (size_t)kNumBuckets * 8);
   cells.deps = reinterpret_cast<int*>(A + L.off_deps);
   cells.down = reinterpret_cast<unsigned*>(A + L.off_down);
+  cells.lev_perm = polish ? reinterpret_cast<unsigned short*>(A + L.off_lev_perm) : nullptr;
+  cells.lev_off = polish ? reinterpret_cast<unsigned short*>(A + L.off_lev_off) : nullptr;
+  cells.lev_depth = polish ? reinterpret_cast<int*>(A + L.off_lev_depth) : nullptr;
   Control* dctl = reinterpret_cast<Control*>(A + L.off_ctl);
 
   CK(cudaEventRecord(ex.ev[0], st));
@@ -512,6 +521,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.relaxed = ctx->opts.queue_order;
   p.gated = 0;
   p.cell_key = ctx->opts.cell_key;
+  p.use_levels = 0;
   CK(cudaEventRecord(ex.ev[1], st));
   int grid_ctas = 0;
   CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas));
@@ -524,6 +534,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     p.pass = 1;
     p.kappa_from_ctl = 0;
     p.gated = 1;
+    p.use_levels = 1;
     CK(cudaEventRecord(ex.ev[3], st));
     // monotone FP64 sweeps down from the lifted FP32 result
     CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr));
@@ -535,6 +546,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
                             L.total_cells, cells, dctl, tol, st));
     p.pass = 2;
     p.gated = 0;
+    p.use_levels = 0;
     CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
   }
   CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), segs, dctl,
@@ -610,6 +622,8 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
       stats->phase_seconds[ps][2] = hres->counters[ps][kCntSweepNs] * 1e-9;
       stats->phase_seconds[ps][3] = hres->counters[ps][kCntFlagNs] * 1e-9;
       stats->revisits[ps] = hres->counters[ps][kCntRevisits];
+      stats->revisit_sweeps[ps] = hres->counters[ps][kCntRevisitSweeps];
+      stats->revisit_updates[ps] = hres->counters[ps][kCntRevisitUpdates];
     }
     for (int ps = 0; ps < 3; ++ps) stats->max_visit_sweeps[ps] = hres->counters[ps][kCntMaxSweeps];
     stats->precision_used = polish ? EIK_FP32_POLISH : EIK_FP64;

@@ -109,7 +109,12 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
 // by more than the threshold activate the neighbours that may now use it.
 // `left` records, per axis (bit 0 x, 1 y, 2 z), an activation on the plane
 // the sweep has just left.
-template <typename T, int N, bool REPLACE>
+// ATOMIC: the level pass, where nodes of one level may be grid neighbours:
+// the node's own active bit is cleared before its neighbours are read, an
+// activation is published after the new value, and the flag words are
+// changed with atomics.  A neighbour that is updated concurrently then either
+// reads the new value or stays active for a later sweep.
+template <typename T, int N, bool REPLACE, bool ATOMIC = false>
 __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
                                             unsigned* __restrict__ chg, int si, int fx, int fy,
                                             int fz, T kappa, unsigned& n_updates,
@@ -117,7 +122,18 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
   using G = Geo<T, N>;
   const int i = si % N, j = (si / N) % N, k = si / (N * N);
   const T s = S[si];
-  unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
+  unsigned c1;
+  if constexpr (ATOMIC) {
+    atomicAnd(chg + si, ~kActive);  // Alg. 2 l.4
+    __threadfence_block();
+    c1 = 0u;
+  } else {
+    c1 = chg[si] & ~kActive;  // Alg. 2 l.4
+  }
+  auto activate = [&](int nb) {
+    if constexpr (ATOMIC) atomicOr(chg + nb, kActive);
+    else chg[nb] |= kActive;
+  };
   if (s < tinf<T>()) {
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
     const T v = U[t];
@@ -146,37 +162,98 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
       }
     }
     if (big) {
+      if constexpr (ATOMIC) __threadfence_block();
       // Alg. 2 l.8-10: neighbours (in this cell) that may now use the new
       // value become active; neighbours in other cells are reached through
-      // the face flags.  The neighbour on the side the sweep came from lies
-      // on the previous plane.
-      if (i > 0 && (REPLACE || xm > nv)) {
-        chg[si - 1] |= kActive;
+      // the face flags.  In min mode a neighbour y can use the new value only
+      // if it is below y's own value and below y's other neighbour on the
+      // same axis (else that one stays y's axis minimum, and a later change
+      // of it activates y itself).  The neighbour on the side the sweep
+      // came from lies on the previous plane.
+      auto uses = [&](T y, int far) { return REPLACE || (vlt(nv, y) && vlt(nv, U[far])); };
+      if (i > 0 && uses(xm, t - 2)) {
+        activate(si - 1);
         left |= fx == 0 ? 1u : 0u;
       }
-      if (i < N - 1 && (REPLACE || xp > nv)) {
-        chg[si + 1] |= kActive;
+      if (i < N - 1 && uses(xp, t + 2)) {
+        activate(si + 1);
         left |= fx != 0 ? 1u : 0u;
       }
-      if (j > 0 && (REPLACE || ym > nv)) {
-        chg[si - N] |= kActive;
+      if (j > 0 && uses(ym, t - 2 * G::SY)) {
+        activate(si - N);
         left |= fy == 0 ? 2u : 0u;
       }
-      if (j < N - 1 && (REPLACE || yp > nv)) {
-        chg[si + N] |= kActive;
+      if (j < N - 1 && uses(yp, t + 2 * G::SY)) {
+        activate(si + N);
         left |= fy != 0 ? 2u : 0u;
       }
-      if (k > 0 && (REPLACE || zm > nv)) {
-        chg[si - N * N] |= kActive;
+      if (k > 0 && uses(zm, t - 2 * G::SZ)) {
+        activate(si - N * N);
         left |= fz == 0 ? 4u : 0u;
       }
-      if (k < N - 1 && (REPLACE || zp > nv)) {
-        chg[si + N * N] |= kActive;
+      if (k < N - 1 && uses(zp, t + 2 * G::SZ)) {
+        activate(si + N * N);
         left |= fz != 0 ? 4u : 0u;
       }
     }
   }
-  chg[si] = c1;
+  if constexpr (ATOMIC) {
+    if (c1) atomicOr(chg + si, c1);
+  } else {
+    chg[si] = c1;
+  }
+}
+
+// One pass over a cell's nodes in the level order of its table (see
+// polish_levels_kernel): level by level, the active nodes of a level
+// together.  A node's FP32 upwind neighbours have smaller levels, so where
+// the FP64 values keep the FP32 order one pass settles the cell; a node
+// whose FP64 inflow comes from a later node is left active for the sweeps
+// that follow.  Table entries are read from global memory, the next
+// level's while the current one runs.
+template <typename T, int N, int WPC>
+__device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restrict__ S,
+                                           unsigned* __restrict__ chg,
+                                           const unsigned short* __restrict__ perm,
+                                           const unsigned short* __restrict__ loff, int depth,
+                                           int tid, int worker, T kappa, unsigned& n_updates) {
+  constexpr int NT = WPC * 32;
+  constexpr int UNR = 2;
+  constexpr unsigned kNone = 0xffffu;
+  unsigned left = 0;
+  int lo = loff[0], hi = loff[1];
+  unsigned nxt[UNR];
+#pragma unroll
+  for (int h = 0; h < UNR; ++h) {
+    const int e = lo + tid + h * NT;
+    nxt[h] = e < hi ? (unsigned)perm[e] : kNone;
+  }
+  for (int l = 0; l < depth; ++l) {
+    unsigned cur[UNR];
+#pragma unroll
+    for (int h = 0; h < UNR; ++h) cur[h] = nxt[h];
+    const int clo = lo, chi = hi;
+    if (l + 1 < depth) {
+      lo = hi;
+      hi = loff[l + 2];
+#pragma unroll
+      for (int h = 0; h < UNR; ++h) {
+        const int e = lo + tid + h * NT;
+        nxt[h] = e < hi ? (unsigned)perm[e] : kNone;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < UNR; ++h)
+      if (cur[h] != kNone && (chg[cur[h] & (unsigned)(N * N * N - 1)] & kActive))
+        update_node<T, N, false, true>(U, S, chg, (int)cur[h], 0, 0, 0, kappa, n_updates, left);
+    // a level larger than the prefetched slots
+    for (int e = clo + tid + UNR * NT; e < chi; e += NT) {
+      const int si = perm[e];
+      if (chg[si] & kActive)
+        update_node<T, N, false, true>(U, S, chg, si, 0, 0, 0, kappa, n_updates, left);
+    }
+    worker_sync<WPC>(worker);
+  }
 }
 
 // Worker-wide OR of the three axis bits.
@@ -388,6 +465,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   unsigned phase = 0;
   unsigned slot = 0;  // ring slot of the bucket the current cell came from
   unsigned long long n_visits = 0, n_sweeps = 0, n_pushes = 0, busy_ns = 0, n_revisits = 0;
+  unsigned long long rv_sweeps = 0, rv_upd = 0;
   unsigned long long pop_ns = 0, stage_ns = 0, sweep_ns = 0, flag_ns = 0;
   unsigned n_updates = 0;
   unsigned long long upd_total = 0;
@@ -499,6 +577,20 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     bool all_active = !revisit;  // every node active: no need to look
     int dlast = -1;
     unsigned lm = 0;
+    if constexpr (!REPLACE && sizeof(T) == 8) {
+      // polish: one pass in the level order read off the FP32 result first;
+      // the sweeps below only pick up what it left active
+      if (p.use_levels) {
+        const int depth = cells.lev_depth[cell];
+        if (depth > 0) {
+          level_pass<T, N, WPC>(U, S, chg, cells.lev_perm + (size_t)cell * G::N3,
+                                cells.lev_off + (size_t)cell * (kMaxLevels + 1), depth, tid,
+                                worker, kappa, n_updates);
+          ++nsw;
+          all_active = false;
+        }
+      }
+    }
     auto run = [&](int d) {
       int first = 0, last = G::NPLANES - 1;
       if (!all_active) active_planes<N, WPC>(chg, d, tid, worker, wshared + 12, first, last);
@@ -525,6 +617,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       if (!lm) converged = true;
     }
     upd_total += n_updates;
+    if (revisit) rv_upd += n_updates;
     n_updates = 0;
     if (tid == 0) {
       if (converged) atomicOr(cells.dir + cell, kDirVisited);
@@ -660,6 +753,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       // the watchdog only needs to see that visits complete: publish every 8th
       if ((n_visits & 7u) == 1u) atomicAdd(&ctl->progress, 8u);
       n_sweeps += (unsigned long long)nsw;
+      if (revisit) rv_sweeps += (unsigned long long)nsw;
       if (nsw > max_sweeps_seen) max_sweeps_seen = nsw;
     }
   }
@@ -667,10 +761,12 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   // counters
   unsigned long long* cnt = ctl->counters[p.pass];
   if (upd_total) atomicAdd(cnt + kCntUpdates, upd_total);
+  if (rv_upd) atomicAdd(cnt + kCntRevisitUpdates, rv_upd);
   if (tid == 0) {
     if (n_visits) atomicAdd(cnt + kCntVisits, n_visits);
     if (n_sweeps) atomicAdd(cnt + kCntSweeps, n_sweeps);
     if (n_revisits) atomicAdd(cnt + kCntRevisits, n_revisits);
+    if (rv_sweeps) atomicAdd(cnt + kCntRevisitSweeps, rv_sweeps);
     if (max_sweeps_seen) atomicMax(cnt + kCntMaxSweeps, (unsigned long long)max_sweeps_seen);
     if (busy_ns) atomicAdd(cnt + kCntBusyNs, busy_ns);
     atomicAdd(cnt + kCntPopNs, pop_ns);

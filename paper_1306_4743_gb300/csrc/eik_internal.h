@@ -50,6 +50,8 @@ enum CounterIndex {
   kCntFlagNs,     //               write-back and flags
   kCntPopNs,      // time spent in the pop loop (waiting included)
   kCntRevisits,   // visits of a cell that had converged before
+  kCntRevisitSweeps,   // ... their sweeps
+  kCntRevisitUpdates,  // ... their node updates
   kNumCounters
 };
 
@@ -103,7 +105,17 @@ struct CellArrays {
   // Polish schedule (dependency graph read off the FP32 result):
   int* deps;                     // upwind neighbours still to finish a first visit
   unsigned* down;                // bits 0-5: downwind faces; bit 8: first visit done
+  // Level order of each cell's nodes, read off the FP32 result (polish):
+  // lev_perm[g * n^3 ...] the cell's node indices sorted by level,
+  // lev_off[g * (kMaxLevels + 1) + l] the first entry of level l, and
+  // lev_depth[g] the number of levels (0: no table, sweep as usual).
+  unsigned short* lev_perm;
+  unsigned short* lev_off;
+  int* lev_depth;
 };
+
+// Longest chain of in-cell upwind neighbours a level table can hold.
+constexpr int kMaxLevels = 255;
 
 struct CellKernelParams {
   const Instance* inst;
@@ -120,6 +132,7 @@ struct CellKernelParams {
   int relaxed;                      // 1: move past a bucket once its stack is empty
   int gated;                        // 1: polish schedule (cells wait for deps == 0)
   int cell_key;                     // 0: Eq. 3 cell values, 1: Eq. 4 (no reset on pop)
+  int use_levels;                   // 1: start each visit with a pass in level order
 };
 
 }  // namespace eik

@@ -268,6 +268,9 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   cells.run = reinterpret_cast<int*>(A + off_heads + (size_t)kNumBuckets * 8);
   cells.deps = reinterpret_cast<int*>(A + off_deps);
   cells.down = reinterpret_cast<unsigned*>(A + off_down);
+  cells.lev_perm = nullptr;  // FP64 only: no level tables
+  cells.lev_off = nullptr;
+  cells.lev_depth = nullptr;
   Control* dctl = reinterpret_cast<Control*>(A + off_ctl);
 
   CKN(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + off_prep), segs, (int)ncells,
@@ -288,6 +291,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.relaxed = 1;
   p.gated = 0;
   p.cell_key = 0;
+  p.use_levels = 0;
   int grid = 0;
   CKN(launch_cells(true, false, n, p, slot->sms, st, &grid));
   CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), segs, dctl,

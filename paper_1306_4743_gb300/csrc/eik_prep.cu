@@ -446,6 +446,111 @@ __global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi,
   }
 }
 
+// Level tables of the polish (FP32 result -> per-cell node order).  In a
+// cell, node x's in-cell upwind neighbours are those that enter its local
+// solve of Eq. 2 under the FP32 values: along each axis the smaller
+// neighbour, if it is below U32(x) (both when they tie).  The level of x is
+// the length of the longest chain of in-cell upwind neighbours ending at x,
+// so a node's upwind neighbours all have smaller levels and the nodes of one
+// level can be updated together.  A cell whose chains are longer than
+// kMaxLevels gets no table (depth 0) and is swept as usual.
+__global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int total_cells,
+                                     CellArrays c) {
+  __shared__ unsigned char up[4096];   // bit 2a: -axis a neighbour upwind, 2a + 1: +axis a
+  __shared__ unsigned char lev[4096];
+  __shared__ int hist[kMaxLevels + 1];
+  __shared__ int flag, depth_s;
+  // one cell per block, so that many cells are in flight on every SM
+  for (int g = blockIdx.x; g < total_cells; g += gridDim.x) {
+    const PolishInstance P = pi[c.inst[g]];
+    const int N = P.n, N3 = N * N * N, lg = __ffs(N) - 1, nm = N - 1;
+    const float* u32 = static_cast<const float*>(P.u32);
+    const double* s64 = static_cast<const double*>(P.s64);
+    const long long sy = P.px32, sz = P.px32 * P.py;
+    const int lc = g - P.cell_base;
+    const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
+    for (int r = threadIdx.x; r < N3; r += blockDim.x) {
+      const int a = r & nm, b = (r >> lg) & nm, cc = r >> (2 * lg);
+      unsigned m = 0;
+      if (s64[(long long)lc * N3 + r] < CUDART_INF) {
+        const long long t = (long long)(N * cx + a + 1) + sy * (N * cy + b + 1) + sz * (N * cz + cc + 1);
+        const float v = u32[t];
+        const int co[3] = {a, b, cc};
+        const long long st[3] = {1, sy, sz};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          const float lo = u32[t - st[ax]], hi = u32[t + st[ax]];
+          if (co[ax] > 0 && lo < v && lo <= hi) m |= 1u << (2 * ax);
+          if (co[ax] < N - 1 && hi < v && hi <= lo) m |= 1u << (2 * ax + 1);
+        }
+      }
+      up[r] = (unsigned char)m;
+      lev[r] = 0;
+    }
+    __syncthreads();
+    // longest chains by relaxation: levels only grow, so the pass that
+    // changes nothing ends it (at most depth + 1 passes)
+    int passes = 0;
+    for (;;) {
+      if (threadIdx.x == 0) flag = 0;
+      __syncthreads();
+      int ch = 0;
+      for (int r = threadIdx.x; r < N3; r += blockDim.x) {
+        const unsigned m = up[r];
+        if (!m) continue;
+        int l = 0;
+        if (m & 1u) l = max(l, lev[r - 1] + 1);
+        if (m & 2u) l = max(l, lev[r + 1] + 1);
+        if (m & 4u) l = max(l, lev[r - N] + 1);
+        if (m & 8u) l = max(l, lev[r + N] + 1);
+        if (m & 16u) l = max(l, lev[r - N * N] + 1);
+        if (m & 32u) l = max(l, lev[r + N * N] + 1);
+        if (l > lev[r]) {
+          lev[r] = (unsigned char)(l < kMaxLevels ? l : kMaxLevels);
+          ch = 1;
+        }
+      }
+      if (ch) flag = 1;
+      __syncthreads();
+      const int any = flag;
+      __syncthreads();
+      if (!any || ++passes > kMaxLevels) break;
+    }
+    int dmax = 0;
+    for (int r = threadIdx.x; r < N3; r += blockDim.x) dmax = max(dmax, (int)lev[r]);
+    dmax = block_reduce(dmax, MaxOp());
+    if (threadIdx.x == 0) depth_s = dmax + 1;
+    __syncthreads();
+    const int depth = depth_s;
+    if (depth >= kMaxLevels || passes > kMaxLevels) {
+      if (threadIdx.x == 0) c.lev_depth[g] = 0;
+      __syncthreads();
+      continue;
+    }
+    for (int l = threadIdx.x; l <= depth; l += blockDim.x) hist[l] = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < N3; r += blockDim.x) atomicAdd(&hist[lev[r]], 1);
+    __syncthreads();
+    unsigned short* off = c.lev_off + (size_t)g * (kMaxLevels + 1);
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int l = 0; l < depth; ++l) {
+        const int k = hist[l];
+        hist[l] = acc;
+        off[l] = (unsigned short)acc;
+        acc += k;
+      }
+      off[depth] = (unsigned short)acc;
+      c.lev_depth[g] = depth;
+    }
+    __syncthreads();
+    unsigned short* perm = c.lev_perm + (size_t)g * N3;
+    for (int r = threadIdx.x; r < N3; r += blockDim.x)
+      perm[atomicAdd(&hist[lev[r]], 1)] = (unsigned short)r;
+    __syncthreads();
+  }
+}
+
 // Queue the cells that wait for nothing.
 __global__ void seed_ready_kernel(int total_cells, CellArrays c, Control* ctl) {
   if (ctl->status) return;
@@ -626,6 +731,8 @@ cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& g, in
                                                               ctl, 0, 0.0);
   polish_graph_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c,
                                                                cells);
+  if (cells.lev_depth)
+    polish_levels_kernel<<<(unsigned)total_cells, 256, 0, st>>>(d_pi, total_cells, cells);
   setup_polish_kernel<<<1, 32, 0, st>>>(ctl, 0, 0.0);
   seed_ready_kernel<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(total_cells, cells,
                                                                           ctl);

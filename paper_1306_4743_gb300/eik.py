@@ -70,6 +70,8 @@ class Stats(ctypes.Structure):
                 ("fallback_visits", ctypes.c_uint64),
                 ("phase_seconds", (ctypes.c_double * 4) * 2),
                 ("revisits", ctypes.c_uint64 * 2),
+                ("revisit_sweeps", ctypes.c_uint64 * 2),
+                ("revisit_updates", ctypes.c_uint64 * 2),
                 ("max_visit_sweeps", ctypes.c_uint64 * 3),
                 ("seconds_stage", ctypes.c_double * 3)]
 
@@ -79,7 +81,7 @@ class Stats(ctypes.Structure):
             v = getattr(self, name)
             if name == "phase_seconds":
                 v = [[v[i][j] for j in range(4)] for i in range(2)]
-            elif name in ("revisits", "max_visit_sweeps"):
+            elif name in ("revisits", "max_visit_sweeps", "revisit_sweeps", "revisit_updates"):
                 v = [int(x) for x in v]
             elif name == "seconds_stage":
                 v = [float(x) for x in v]

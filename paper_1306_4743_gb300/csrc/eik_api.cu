@@ -206,7 +206,7 @@ void make_plan(LaunchPlan& L, int count, const int64_t* dims, const double* h, i
     L.off_lev_off = take(cur, (size_t)cells * (kMaxLevels + 1) * 2);
     L.off_lev_depth = take(cur, (size_t)cells * 4);
   }
-  L.off_heads = take(cur, (size_t)kNumBuckets * 12);  // heads, then run counts
+  L.off_heads = take(cur, (size_t)kQueueBytes);  // heads, then counts and run counts
   // small tables, filled on the host and copied in one transfer
   L.small_begin = align_up(cur, 256);
   L.off_ctl = take(cur, sizeof(Control));
@@ -479,7 +479,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   }
   CK(cudaMemcpyAsync(A + L.small_begin, hs, L.small_end - L.small_begin, cudaMemcpyHostToDevice,
                      st));
-  CK(cudaMemsetAsync(A + L.off_heads, 0, (size_t)kNumBuckets * 12, st));
+  CK(cudaMemsetAsync(A + L.off_heads, 0, (size_t)kQueueBytes, st));
 
   CellArrays cells;
   cells.key = reinterpret_cast<unsigned*>(A + L.off_key);
@@ -488,7 +488,8 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   cells.inst = reinterpret_cast<int*>(A + L.off_inst);
   cells.next = reinterpret_cast<unsigned*>(A + L.off_next);
   cells.heads = reinterpret_cast<unsigned long long*>(A + L.off_heads);
-  cells.run = reinterpret_cast<int*>(A + L.off_heads + (size_t)kNumBuckets * 8);
+  cells.cnt = reinterpret_cast<int*>(A + L.off_heads + (size_t)kNumBuckets * kSubStacks * 8);
+  cells.run = cells.cnt + kNumBuckets;
   cells.deps = reinterpret_cast<int*>(A + L.off_deps);
   cells.down = reinterpret_cast<unsigned*>(A + L.off_down);
   cells.lev_perm = polish ? reinterpret_cast<unsigned short*>(A + L.off_lev_perm) : nullptr;

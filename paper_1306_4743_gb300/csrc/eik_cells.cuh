@@ -478,7 +478,8 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     unsigned long long t_pop0 = 0;
     if (tid == 0) t_pop0 = global_timer_ns();
     if (wwarp == 0) {
-      cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane, &slot, p.relaxed != 0);
+      cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane, &slot, p.relaxed != 0,
+                            (unsigned)(blockIdx.x * WORKERS + worker) * 7u);
       if (lane == 0 && cell >= 0) {
         // V^c <- +inf (Alg. 1 l.5); the Eq. 4 variant keeps it (Sec. 7)
         if (p.cell_key == 0) atomicExch(cells.key + cell, kKeyInf);

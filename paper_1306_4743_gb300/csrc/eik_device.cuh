@@ -38,6 +38,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -391,19 +396,30 @@ __device__ __forceinline__ double tinf<double>() { return CUDART_INF; }
 //
 // Bucket b (an absolute, ever-growing index) holds cells whose key lies in
 // [base + b/inv_width, base + (b+1)/inv_width); it lives in ring slot
-// b mod kNumBuckets as a lock-free stack (Treiber stack with a 32-bit ABA
-// tag in the head word).  `cur` is the bucket being processed.  Workers
-// take cells only from bucket `cur`, and `cur` moves on only when its stack
-// is empty AND no cell taken from it is still being swept (run[slot] == 0):
-// the buckets are processed in order, like the heap of Alg. 1 processes
-// cells in order of their values, while all cells of one bucket run in
-// parallel.  A push into a lower bucket lowers `cur` (atomicMin).  A worker
-// that moves `cur` forward re-checks the buckets it skipped, so a push that
-// raced the move is not stranded.  Within a bucket the order is arbitrary;
-// the final values do not depend on the processing order (Sec. 4).
+// b mod kNumBuckets as kSubStacks lock-free stacks (Treiber stacks with a
+// 32-bit ABA tag in the head word) and a count of the cells in it.  A push
+// picks a sub-stack by a hash of the cell id and a popping warp reads all
+// sub-stack heads at once (a lane each), starting its choice at a
+// worker-specific one, so the compare-and-swaps of several hundred workers
+// spread over 32 words instead of queueing on one.  `cur` is the bucket
+// being processed.  Workers take cells only from bucket `cur`, and `cur`
+// moves on only when its count is zero AND no cell taken from it is still
+// being swept (run[slot] == 0): the buckets are processed in order, like the
+// heap of Alg. 1 processes cells in order of their values, while all cells
+// of one bucket run in parallel.  A push into a lower bucket lowers `cur`
+// (atomicMin).  The count rises before the cell is linked in and falls after
+// it is unlinked, so a zero count means an empty bucket; a worker that moves
+// `cur` forward re-checks the buckets it skipped, so a push that raced the
+// move is not stranded.  Within a bucket the order is arbitrary; the final
+// values do not depend on the processing order (Sec. 4).
 
-__device__ __forceinline__ void stack_push(const CellArrays& c, unsigned slot, unsigned cell) {
-  unsigned long long* head = c.heads + slot;
+__device__ __forceinline__ unsigned long long* sub_head(const CellArrays& c, unsigned slot,
+                                                        unsigned sub) {
+  return c.heads + (size_t)slot * kSubStacks + sub;
+}
+
+__device__ __forceinline__ void stack_push(unsigned long long* head, const CellArrays& c,
+                                           unsigned cell) {
   unsigned long long old = ld_relaxed_u64(head);
   for (;;) {
     c.next[cell] = (unsigned)(old & 0xffffffffull);
@@ -415,10 +431,10 @@ __device__ __forceinline__ void stack_push(const CellArrays& c, unsigned slot, u
   }
 }
 
-// Returns the popped cell or -1 when the stack is empty.
-__device__ __forceinline__ int stack_pop(const CellArrays& c, unsigned slot) {
-  unsigned long long* head = c.heads + slot;
-  unsigned long long old = ld_acquire_u64(head);
+// Returns the popped cell or -1 when the sub-stack is empty; `old` is a
+// recent value of its head.
+__device__ __forceinline__ int stack_pop(unsigned long long* head, const CellArrays& c,
+                                         unsigned long long old) {
   for (;;) {
     const unsigned top = (unsigned)(old & 0xffffffffull);
     if (top == 0) return -1;
@@ -434,8 +450,8 @@ __device__ __forceinline__ int stack_pop(const CellArrays& c, unsigned slot) {
   }
 }
 
-__device__ __forceinline__ bool stack_empty(const CellArrays& c, unsigned slot) {
-  return (unsigned)(ld_acquire_u64(c.heads + slot) & 0xffffffffull) == 0u;
+__device__ __forceinline__ bool bucket_empty(const CellArrays& c, unsigned slot) {
+  return ld_acquire_s32(c.cnt + slot) <= 0;
 }
 
 __device__ __forceinline__ unsigned bucket_of(const Control* ctl, float keyf, unsigned cur) {
@@ -454,8 +470,10 @@ __device__ __forceinline__ void queue_push(const CellArrays& c, Control* ctl, un
   const unsigned cur = ld_relaxed_u32(&ctl->cur);
   const float keyf = float_of_ord(ld_relaxed_u32(c.key + cell));
   const unsigned b = bucket_of(ctl, keyf, cur);
+  const unsigned slot = b & kBucketMask;
   atomicAdd(&ctl->queued, 1);
-  stack_push(c, b & kBucketMask, cell);
+  atomicAdd(c.cnt + slot, 1);
+  stack_push(sub_head(c, slot, (cell * 0x9E3779B1u) >> (32 - kSubStackBits)), c, cell);
   __threadfence();
   atomicMin(&ctl->cur, b);
   ++*pushes;
@@ -473,8 +491,7 @@ __device__ __forceinline__ int scan_next_bucket(const CellArrays& c, unsigned cu
     for (int r = 0; r < 4; ++r) {
       const int o = base + r * 32 + lane;
       const bool ne = o < kNumBuckets &&
-                      (unsigned)(ld_relaxed_u64(c.heads + ((cur + (unsigned)o) & kBucketMask)) &
-                                 0xffffffffull) != 0u;
+                      ld_relaxed_s32(c.cnt + ((cur + (unsigned)o) & kBucketMask)) > 0;
       const unsigned bal = __ballot_sync(0xffffffffu, ne);
       if (bal && m == 0) m = (unsigned)(base + r * 32 + __ffs(bal) - 1);
     }
@@ -485,64 +502,86 @@ __device__ __forceinline__ int scan_next_bucket(const CellArrays& c, unsigned cu
 
 // Warp-collective pop (all 32 lanes of the calling warp).  Returns a cell
 // whose state is now RUNNING (and the ring slot it came from in *slot_out),
-// or -1 when the solve is finished or failed.
+// or -1 when the solve is finished or failed.  `rot` picks the sub-stack the
+// warp tries first.
 static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
                                      unsigned long long spin_cap_ns, int lane,
-                                     unsigned* slot_out, bool relaxed) {
+                                     unsigned* slot_out, bool relaxed, unsigned rot) {
   unsigned last_prog = 0xffffffffu;
   unsigned long long t_idle = 0;
   unsigned backoff = 64;
   unsigned polls = 0;
+  const unsigned sub = (lane + rot) & (kSubStacks - 1);
   for (;;) {
     int stop = 0, cell = -1, can_advance = 0;
     unsigned cur = 0;
+    // The fast path of a poll reads cur and the sub-stack heads of its
+    // bucket; termination, errors and bucket completion are checked every
+    // 4th empty poll, to keep the traffic of waiting workers on the shared
+    // control words low.
+    const bool full_check = (polls & 3u) == 0u;
     if (lane == 0) {
-      // The fast path of a poll reads two words (cur and its stack head);
-      // termination, errors and bucket completion are checked every 4th
-      // empty poll, to keep the traffic of waiting workers on the shared
-      // control words low.
-      const bool full_check = (polls & 3u) == 0u;
       if (full_check)
         stop = (ld_acquire_s32(&ctl->status) != 0) || (ld_acquire_s32(&ctl->active) <= 0);
-      if (!stop) {
-        cur = ld_acquire_u32(&ctl->cur);
-        const unsigned slot = cur & kBucketMask;
-        if (!stack_empty(c, slot)) {
-          atomicAdd(c.run + slot, 1);  // reserve before taking: blocks an advance
-          cell = stack_pop(c, slot);
-          if (cell < 0) {
-            atomicSub(c.run + slot, 1);
-          } else {
-            atomicSub(&ctl->queued, 1);
-            // QUEUED -> RUNNING (drops DIRTY: this visit loads the newest data)
-            unsigned st = ld_relaxed_u32(c.state + cell);
-            for (;;) {
-              if (!(st & kStQueued)) {
-                set_status(ctl, EIK_EQUEUE);
-                cell = -1;
-                stop = 1;
-                break;
-              }
-              const unsigned prev = atomicCAS(c.state + cell, st, kStRunning);
-              if (prev == st) break;
-              st = prev;
-            }
-            __threadfence();
-            *slot_out = slot;
-          }
-        } else if (full_check) {
-          // strict order: the bucket is done when no cell taken from it is
-          // still running; relaxed order: as soon as its stack is empty
-          can_advance = (relaxed || ld_acquire_s32(c.run + slot) == 0) && stack_empty(c, slot);
-        }
-      }
-      ++polls;
+      if (!stop) cur = ld_acquire_u32(&ctl->cur);
     }
     stop = __shfl_sync(0xffffffffu, stop, 0);
     if (stop) return -1;
-    cell = __shfl_sync(0xffffffffu, cell, 0);
-    if (cell >= 0) return cell;
     cur = __shfl_sync(0xffffffffu, cur, 0);
+    const unsigned slot = cur & kBucketMask;
+    unsigned long long* head = sub_head(c, slot, sub);
+    const unsigned long long h = ld_acquire_u64(head);
+    unsigned ne = __ballot_sync(0xffffffffu, (h & 0xffffffffull) != 0ull);
+    if (ne) {
+      if (lane == 0) atomicAdd(c.run + slot, 1);  // reserve before taking: blocks an advance
+      __syncwarp();
+      while (ne) {
+        const int l = __ffs(ne) - 1;
+        int got = -1;
+        if (lane == l) got = stack_pop(head, c, h);
+        got = __shfl_sync(0xffffffffu, got, l);
+        if (got >= 0) {
+          cell = got;
+          break;
+        }
+        ne &= ne - 1u;
+      }
+      if (lane == 0) {
+        if (cell < 0) {
+          atomicSub(c.run + slot, 1);
+        } else {
+          atomicSub(c.cnt + slot, 1);
+          atomicSub(&ctl->queued, 1);
+          // QUEUED -> RUNNING (drops DIRTY: this visit loads the newest data)
+          unsigned st = ld_relaxed_u32(c.state + cell);
+          for (;;) {
+            if (!(st & kStQueued)) {
+              set_status(ctl, EIK_EQUEUE);
+              cell = -1;
+              stop = 1;
+              break;
+            }
+            const unsigned prev = atomicCAS(c.state + cell, st, kStRunning);
+            if (prev == st) break;
+            st = prev;
+          }
+          __threadfence();
+          *slot_out = slot;
+        }
+      }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (stop) return -1;
+      cell = __shfl_sync(0xffffffffu, cell, 0);
+      if (cell >= 0) return cell;
+      ++polls;
+      continue;  // lost every race: look again at once
+    }
+    if (lane == 0 && full_check) {
+      // strict order: the bucket is done when no cell taken from it is
+      // still running; relaxed order: as soon as it is empty
+      can_advance = (relaxed || ld_acquire_s32(c.run + slot) == 0) && bucket_empty(c, slot);
+    }
+    ++polls;
     can_advance = __shfl_sync(0xffffffffu, can_advance, 0);
 
     if (can_advance) {
@@ -558,7 +597,7 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
             if (atomicCAS(&ctl->cur, cur, cur + (unsigned)found) == cur) {
               __threadfence();
               for (int o = 0; o < found; ++o) {
-                if (!stack_empty(c, (cur + (unsigned)o) & kBucketMask)) {
+                if (!bucket_empty(c, (cur + (unsigned)o) & kBucketMask)) {
                   atomicMin(&ctl->cur, cur + (unsigned)o);
                   break;
                 }
@@ -590,7 +629,7 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
     timed_out = __shfl_sync(0xffffffffu, timed_out, 0);
     if (timed_out) return -1;
     __nanosleep(backoff);
-    if (backoff < 16384) backoff *= 2;
+    if (backoff < 2048) backoff *= 2;
   }
 }
 

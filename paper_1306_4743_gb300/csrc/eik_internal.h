@@ -19,9 +19,13 @@
 
 namespace eik {
 
-// Dial bucket ring: 4096 buckets, each a lock-free stack of cells.
+// Dial bucket ring: 4096 buckets, each 32 lock-free stacks of cells.
 constexpr int kNumBuckets = 4096;
 constexpr unsigned kBucketMask = kNumBuckets - 1;
+constexpr int kSubStackBits = 5;
+constexpr int kSubStacks = 1 << kSubStackBits;
+// device bytes of the queue: sub-stack heads, then counts and run counts
+constexpr unsigned long long kQueueBytes = (unsigned long long)kNumBuckets * (kSubStacks * 8 + 8);
 
 // Cell state bits.
 constexpr unsigned kStQueued = 1u;   // in exactly one bucket stack
@@ -100,7 +104,8 @@ struct CellArrays {
   unsigned* dir;                 // preferred sweep directions, 8 bits
   int* inst;                     // instance of each cell
   unsigned* next;                // stack links: next cell + 1, 0 = end
-  unsigned long long* heads;     // [kNumBuckets] (tag << 32) | (top cell + 1)
+  unsigned long long* heads;     // [kNumBuckets][kSubStacks] (tag << 32) | (top cell + 1)
+  int* cnt;                      // [kNumBuckets] cells in a bucket (raised before linking)
   int* run;                      // [kNumBuckets] cells taken from a bucket, not retired
   // Polish schedule (dependency graph read off the FP32 result):
   int* deps;                     // upwind neighbours still to finish a first visit

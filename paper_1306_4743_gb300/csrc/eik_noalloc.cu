@@ -133,7 +133,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   const size_t off_next = take(cur, (size_t)ncells * 4);
   const size_t off_deps = take(cur, (size_t)ncells * 4);
   const size_t off_down = take(cur, (size_t)ncells * 4);
-  const size_t off_heads = take(cur, (size_t)kNumBuckets * 12);
+  const size_t off_heads = take(cur, (size_t)kQueueBytes);
   const size_t small_begin = up(cur, 256);
   const size_t off_ctl = take(cur, sizeof(Control));
   const size_t off_nsrc = take(cur, 4);
@@ -256,7 +256,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   // zero fills, so the contents left by the previous call do not matter.
   CKN(cudaMemcpyAsync(A + small_begin, g_host_small, small_end - small_begin,
                       cudaMemcpyHostToDevice, st));
-  CKN(cudaMemsetAsync(A + off_heads, 0, (size_t)kNumBuckets * 12, st));
+  CKN(cudaMemsetAsync(A + off_heads, 0, (size_t)kQueueBytes, st));
 
   CellArrays cells;
   cells.key = reinterpret_cast<unsigned*>(A + off_key);
@@ -265,7 +265,8 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   cells.inst = reinterpret_cast<int*>(A + off_inst);
   cells.next = reinterpret_cast<unsigned*>(A + off_next);
   cells.heads = reinterpret_cast<unsigned long long*>(A + off_heads);
-  cells.run = reinterpret_cast<int*>(A + off_heads + (size_t)kNumBuckets * 8);
+  cells.cnt = reinterpret_cast<int*>(A + off_heads + (size_t)kNumBuckets * kSubStacks * 8);
+  cells.run = cells.cnt + kNumBuckets;
   cells.deps = reinterpret_cast<int*>(A + off_deps);
   cells.down = reinterpret_cast<unsigned*>(A + off_down);
   cells.lev_perm = nullptr;  // FP64 only: no level tables

@@ -245,6 +245,16 @@ __device__ __forceinline__ double f64_of_f32_nn(float x) {
       (long long)(e == 0 ? 0ull : (e == 255 ? 0x7ff0000000000000ull : r)));
 }
 __device__ __forceinline__ bool dlt_nn(double a, double b) { return dbits(a) < dbits(b); }
+// Round-to-nearest narrowing of a double x >= 0 (or +inf) on the integer
+// pipe: the truncation plus one float ulp when the dropped bits are more
+// than half an ulp (ties away from zero; values below the float normal
+// range become 0).
+__device__ __forceinline__ float f32_of_f64_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const float t = f32_of_f64_nn(x);
+  const unsigned up = ((b >> 28) & 1ull) && (b >> 52) > 896 && (b >> 52) < 1151 ? 1u : 0u;
+  return __uint_as_float(__float_as_uint(t) + up);
+}
 
 // A double x >= 0 as hi + lo with hi its leading 24 mantissa bits (the
 // truncation f32_of_f64_nn) and lo the remaining 29 bits rounded to a float:

@@ -155,13 +155,37 @@ __global__ void init_u_kernel(const PrepInstance* __restrict__ pi, const int* __
   }
 }
 
+// |v - lam| for stored values v, lam >= 0 (finite v), from the distance of
+// their bit patterns: D steps of v's ulp, exact when both lie in one binade
+// and at most twice the true distance across a binade boundary (an upper
+// bound, which keeps the fallback test conservative).  Integer pipe and
+// FP32 only; +inf when lam is +inf or D does not fit 32 bits.
+__device__ __forceinline__ double resid_nn(double v, double lam) {
+  const long long iv = __double_as_longlong(v), il = __double_as_longlong(lam);
+  const unsigned long long D = (unsigned long long)(iv > il ? iv - il : il - iv);
+  if (D == 0ull) return 0.0;
+  if (il >= 0x7ff0000000000000ll || (D >> 32)) return CUDART_INF;
+  const int ev = (int)(iv >> 52) > 0 ? (int)(iv >> 52) : 1;
+  const int pe = ev - 1075 + 127;  // ulp(v) = 2^(ev - 1075) as a float exponent
+  if (pe < 1) return 0.0;          // below 2^-126: negligible
+  return f64_of_f32_nn(__uint2float_ru((unsigned)D) * __int_as_float(pe << 23));
+}
+
 // s = h / F in FP64 from an FP32 reciprocal r and two FMA corrections
 // q <- q + r (h - q F): each multiplies the relative error by ~2^-24, so
 // from q0 = h r the result is within an ulp of the correctly rounded
 // quotient, with five FP64 instructions instead of a division.
 __device__ __forceinline__ double slowness(double h, float f) {
-  const double fd = (double)f;
-  const double r = (double)__frcp_rn(f);
+  // f and 1/f widened on the integer pipe while both are normal floats
+  const float rf = __frcp_rn(f);
+  double fd, r;
+  if (__builtin_expect(f >= 1.17549435e-38f && f <= 8.50705917e37f, 1)) {
+    fd = f64_of_f32_nn(f);
+    r = f64_of_f32_nn(rf);
+  } else {
+    fd = (double)f;
+    r = (double)rf;
+  }
   const double q0 = h * r;
   const double q1 = fma(fma(-q0, fd, h), r, q0);
   return fma(fma(-q1, fd, h), r, q1);
@@ -182,7 +206,7 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __
   const int ey = N * P.ncy, ex = N * P.ncx;  // extents covered by the cells
   const long long rows = (long long)ey * N * P.ncz;
   const double qb = q_base(ctl);
-  double acc = 0.0;
+  float acc = 0.0f;  // for the mean of s (bucket width): FP32 is plenty
   unsigned long long cnt = 0;
   int bad = 0;
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -208,12 +232,13 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __
             bad = 1;
           } else {
             sv = slowness(P.h, f);
-            acc += sv;
+            acc += f32_of_f64_nn(sv);
             ++cnt;
           }
         }
       }
-      s[e] = (T)sv;
+      if constexpr (sizeof(T) == 8) s[e] = (T)sv;
+      else s[e] = f32_of_f64_rn(sv);
       if (s64) s64[e] = sv;
     }
   }
@@ -222,7 +247,7 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __
   bad = block_reduce(bad, MaxOp());
   if (threadIdx.x == 0) {
     if (cnt) {
-      atomicAdd(&ctl->sum_s, acc);
+      atomicAdd(&ctl->sum_s, (double)acc);
       atomicAdd(&ctl->n_s, cnt);
     }
     if (bad) atomicExch(&ctl->bad_input, 1);
@@ -300,9 +325,10 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, const in
           // error grows at most ~2^-24 u per node along a characteristic (u
           // is stored relative to q_min), so a lift of 2^-11 u covers paths
           // of up to 2^13 nodes.  The monotone FP64 sweeps then descend to
-          // the fixed point.
-          v = (double)row32[x];
-          v += v * 4.8828125e-4;
+          // the fixed point.  The lift is formed in FP32 (its own rounding,
+          // 2^-24 u, is far inside the margin) and widened on the integer
+          // pipe: no FP64 instruction per node.
+          v = f64_of_f32_nn(row32[x] * 1.00048828125f);
         }
         if (isfinite(v)) {
           const unsigned long long o = ord_of_double(v);
@@ -446,21 +472,22 @@ __global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi,
   }
 }
 
-// Level tables of the polish (FP32 result -> per-cell node order).  In a
-// cell, node x's in-cell upwind neighbours are those that enter its local
-// solve of Eq. 2 under the FP32 values: along each axis the smaller
-// neighbour, if it is below U32(x) (both when they tie).  The level of x is
-// the length of the longest chain of in-cell upwind neighbours ending at x,
-// so a node's upwind neighbours all have smaller levels and the nodes of one
-// level can be updated together.  A cell whose chains are longer than
-// kMaxLevels gets no table (depth 0) and is swept as usual.
+// Level order of each cell's nodes for the first polish visit: a node's
+// in-cell upwind neighbours under the FP32 result (the smaller neighbour
+// on an axis, if below the node; both on an FP32 tie) come first.  Levels
+// are the layers of Kahn's topological order: level 0 holds the nodes with
+// no in-cell upwind neighbour, and a node joins the layer after the one in
+// which its last upwind neighbour was taken (so level = longest upwind
+// chain).  Each layer is appended to the node list in shared memory and
+// becomes a run of lev_perm; lev_off[l] is where layer l starts.  One block
+// per cell; cells deeper than kMaxLevels - 1 get no table (lev_depth 0).
 __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int total_cells,
                                      CellArrays c) {
   __shared__ unsigned char up[4096];   // bit 2a: -axis a neighbour upwind, 2a + 1: +axis a
-  __shared__ unsigned char lev[4096];
-  __shared__ int hist[kMaxLevels + 1];
-  __shared__ int flag, depth_s;
-  // one cell per block, so that many cells are in flight on every SM
+  __shared__ unsigned indeg[1024];     // upwind neighbours not yet taken, a byte per node
+  __shared__ unsigned short lst[4096];  // nodes in level order
+  __shared__ unsigned short offs[kMaxLevels + 1];
+  __shared__ int tail;
   for (int g = blockIdx.x; g < total_cells; g += gridDim.x) {
     const PolishInstance P = pi[c.inst[g]];
     const int N = P.n, N3 = N * N * N, lg = __ffs(N) - 1, nm = N - 1;
@@ -469,6 +496,9 @@ __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int 
     const long long sy = P.px32, sz = P.px32 * P.py;
     const int lc = g - P.cell_base;
     const int cx = lc % P.ncx, cy = (lc / P.ncx) % P.ncy, cz = lc / (P.ncx * P.ncy);
+    if (threadIdx.x == 0) tail = 0;
+    for (int w = threadIdx.x; w < (N3 + 3) / 4; w += blockDim.x) indeg[w] = 0u;
+    __syncthreads();
     for (int r = threadIdx.x; r < N3; r += blockDim.x) {
       const int a = r & nm, b = (r >> lg) & nm, cc = r >> (2 * lg);
       unsigned m = 0;
@@ -485,69 +515,63 @@ __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int 
         }
       }
       up[r] = (unsigned char)m;
-      lev[r] = 0;
+      if (m) {
+        atomicAdd(&indeg[r >> 2], (unsigned)__popc(m) << (8 * (r & 3)));
+      } else {
+        const unsigned act = __activemask();  // warp-aggregated append
+        const int leader = __ffs(act) - 1, lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&tail, __popc(act));
+        base = __shfl_sync(act, base, leader);
+        lst[base + __popc(act & ((1u << lane) - 1u))] = (unsigned short)r;
+      }
     }
     __syncthreads();
-    // longest chains by relaxation: levels only grow, so the pass that
-    // changes nothing ends it (at most depth + 1 passes)
-    int passes = 0;
+    // layer by layer: taking a node releases the neighbours it is upwind of
+    int lo = 0, depth = 0;
+    bool ok = true;
     for (;;) {
-      if (threadIdx.x == 0) flag = 0;
-      __syncthreads();
-      int ch = 0;
-      for (int r = threadIdx.x; r < N3; r += blockDim.x) {
-        const unsigned m = up[r];
-        if (!m) continue;
-        int l = 0;
-        if (m & 1u) l = max(l, lev[r - 1] + 1);
-        if (m & 2u) l = max(l, lev[r + 1] + 1);
-        if (m & 4u) l = max(l, lev[r - N] + 1);
-        if (m & 8u) l = max(l, lev[r + N] + 1);
-        if (m & 16u) l = max(l, lev[r - N * N] + 1);
-        if (m & 32u) l = max(l, lev[r + N * N] + 1);
-        if (l > lev[r]) {
-          lev[r] = (unsigned char)(l < kMaxLevels ? l : kMaxLevels);
-          ch = 1;
+      const int hi = tail;  // this layer: lst[lo, hi)
+      if (hi == lo) break;
+      if (depth >= kMaxLevels) {
+        ok = false;
+        break;
+      }
+      if (threadIdx.x == 0) offs[depth] = (unsigned short)lo;
+      ++depth;
+      __syncthreads();  // everyone has read tail before the appends below
+      for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const int x = lst[e];
+        const int co[3] = {x & nm, (x >> lg) & nm, x >> (2 * lg)};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          const int step = 1 << (lg * ax);
+          // x is the -ax neighbour of y = x + step (y's bit 2 ax) and the
+          // +ax neighbour of y = x - step (y's bit 2 ax + 1)
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const bool inside = side == 0 ? co[ax] < N - 1 : co[ax] > 0;
+            if (!inside) continue;
+            const int y = side == 0 ? x + step : x - step;
+            if (!((up[y] >> (2 * ax + side)) & 1u)) continue;
+            const unsigned sh = 8 * (y & 3);
+            const unsigned old = atomicSub(&indeg[y >> 2], 1u << sh);
+            if (((old >> sh) & 0xffu) == 1u) lst[atomicAdd(&tail, 1)] = (unsigned short)y;
+          }
         }
       }
-      if (ch) flag = 1;
-      __syncthreads();
-      const int any = flag;
-      __syncthreads();
-      if (!any || ++passes > kMaxLevels) break;
+      lo = hi;
+      __syncthreads();  // the next layer is complete
     }
-    int dmax = 0;
-    for (int r = threadIdx.x; r < N3; r += blockDim.x) dmax = max(dmax, (int)lev[r]);
-    dmax = block_reduce(dmax, MaxOp());
-    if (threadIdx.x == 0) depth_s = dmax + 1;
-    __syncthreads();
-    const int depth = depth_s;
-    if (depth >= kMaxLevels || passes > kMaxLevels) {
-      if (threadIdx.x == 0) c.lev_depth[g] = 0;
-      __syncthreads();
-      continue;
+    if (threadIdx.x == 0) c.lev_depth[g] = ok ? depth : 0;
+    if (ok) {
+      unsigned short* off = c.lev_off + (size_t)g * (kMaxLevels + 1);
+      for (int l = threadIdx.x; l < depth; l += blockDim.x) off[l] = offs[l];
+      if (threadIdx.x == 0) off[depth] = (unsigned short)N3;
+      unsigned short* perm = c.lev_perm + (size_t)g * N3;
+      for (int e = threadIdx.x; e < N3; e += blockDim.x) perm[e] = lst[e];
     }
-    for (int l = threadIdx.x; l <= depth; l += blockDim.x) hist[l] = 0;
-    __syncthreads();
-    for (int r = threadIdx.x; r < N3; r += blockDim.x) atomicAdd(&hist[lev[r]], 1);
-    __syncthreads();
-    unsigned short* off = c.lev_off + (size_t)g * (kMaxLevels + 1);
-    if (threadIdx.x == 0) {
-      int acc = 0;
-      for (int l = 0; l < depth; ++l) {
-        const int k = hist[l];
-        hist[l] = acc;
-        off[l] = (unsigned short)acc;
-        acc += k;
-      }
-      off[depth] = (unsigned short)acc;
-      c.lev_depth[g] = depth;
-    }
-    __syncthreads();
-    unsigned short* perm = c.lev_perm + (size_t)g * N3;
-    for (int r = threadIdx.x; r < N3; r += blockDim.x)
-      perm[atomicAdd(&hist[lev[r]], 1)] = (unsigned short)r;
-    __syncthreads();
+    __syncthreads();  // shared arrays are reused by the next cell
   }
 }
 
@@ -639,7 +663,7 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi,
       const long long t = tbase + i;
       const double v = u[t];
       const long long e = rbase + i;
-      P.out[e] = P.mask[e] ? P.q[e] : v + qb;
+      P.out[e] = P.mask[e] ? P.q[e] : (qb == 0.0 ? v : v + qb);
       if (!isfinite(v)) {
         ++nbad;
         continue;
@@ -655,8 +679,7 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi,
       // A value left below the fixed point (lift too small) or above it (a
       // flag skipped on the FP32 error bound) both show here and send the
       // solve to the replace-mode fallback.
-      const double r = fabs(v - lam);
-      const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+      const unsigned long long rb = (unsigned long long)__double_as_longlong(resid_nn(v, lam));
       rmax = rb > rmax ? rb : rmax;
     }
   }

@@ -44,6 +44,9 @@ __device__ __forceinline__ bool vlt(double a, double b) { return dlt_nn(a, b); }
 // the latency of word accesses, and these bits sit on the sweep's
 // critical path.
 constexpr unsigned kWritten = 1, kBig = 2, kActive = 4;
+// level pass of the polish: changed above kappa in the current step,
+// neighbours still to be activated
+constexpr unsigned kStep = 8;
 
 template <typename T, int N>
 struct Geo {
@@ -78,7 +81,13 @@ struct Geo {
   static constexpr int OFF_CHG = OFF_S + align128(SBYTES);
   // active-node list of one plane (at most N^2 nodes lie on a plane)
   static constexpr int OFF_LIST = OFF_CHG + align128(N3 * 4);
-  static constexpr int OFF_BAR = OFF_LIST + align128(N * N * 2);
+  // FP64 only: the cell's level table (node order, level starts), staged
+  // with the cell for the level pass of a first polish visit
+  static constexpr int PERM_BYTES = ES == 8 ? align128(N3 * 2) : 0;
+  static constexpr int LOFF_BYTES = ES == 8 ? align128((kMaxLevels + 1) * 2) : 0;
+  static constexpr int OFF_PERM = OFF_LIST + align128(N * N * 2);
+  static constexpr int OFF_LOFF = OFF_PERM + PERM_BYTES;
+  static constexpr int OFF_BAR = OFF_LOFF + LOFF_BYTES;
   static constexpr int WORKER_BYTES = OFF_BAR + 128;
   // CTA-wide: plane table | plane offsets
   static constexpr int TAB_BYTES = align128(N3 * 2);
@@ -109,12 +118,7 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
 // by more than the threshold activate the neighbours that may now use it.
 // `left` records, per axis (bit 0 x, 1 y, 2 z), an activation on the plane
 // the sweep has just left.
-// ATOMIC: the level pass, where nodes of one level may be grid neighbours:
-// the node's own active bit is cleared before its neighbours are read, an
-// activation is published after the new value, and the flag words are
-// changed with atomics.  A neighbour that is updated concurrently then either
-// reads the new value or stays active for a later sweep.
-template <typename T, int N, bool REPLACE, bool ATOMIC = false>
+template <typename T, int N, bool REPLACE>
 __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
                                             unsigned* __restrict__ chg, int si, int fx, int fy,
                                             int fz, T kappa, unsigned& n_updates,
@@ -122,18 +126,8 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
   using G = Geo<T, N>;
   const int i = si % N, j = (si / N) % N, k = si / (N * N);
   const T s = S[si];
-  unsigned c1;
-  if constexpr (ATOMIC) {
-    atomicAnd(chg + si, ~kActive);  // Alg. 2 l.4
-    __threadfence_block();
-    c1 = 0u;
-  } else {
-    c1 = chg[si] & ~kActive;  // Alg. 2 l.4
-  }
-  auto activate = [&](int nb) {
-    if constexpr (ATOMIC) atomicOr(chg + nb, kActive);
-    else chg[nb] |= kActive;
-  };
+  unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
+  auto activate = [&](int nb) { chg[nb] |= kActive; };
   if (s < tinf<T>()) {
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
     const T v = U[t];
@@ -162,7 +156,6 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
       }
     }
     if (big) {
-      if constexpr (ATOMIC) __threadfence_block();
       // Alg. 2 l.8-10: neighbours (in this cell) that may now use the new
       // value become active; neighbours in other cells are reached through
       // the face flags.  In min mode a neighbour y can use the new value only
@@ -197,20 +190,69 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
       }
     }
   }
-  if constexpr (ATOMIC) {
-    if (c1) atomicOr(chg + si, c1);
-  } else {
-    chg[si] = c1;
+  chg[si] = c1;
+}
+
+// Level-pass helpers (min mode, Alg. 2).  take_node: node si is active and
+// no other thread writes its flag word in this step: clear its active bit,
+// recompute it from its six neighbours (Eq. 2), store a lower value and
+// mark a change above kappa with kStep.  wake_users: for a node marked
+// kStep, clear the mark and activate the neighbours that may now use its
+// value (below the neighbour and below the neighbour's other neighbour on
+// that axis); a neighbour that is still active is left alone.
+template <typename T, int N>
+__device__ __forceinline__ void take_node(T* __restrict__ U, const T* __restrict__ S,
+                                          unsigned* __restrict__ chg, int si, T kappa,
+                                          unsigned& n_updates) {
+  using G = Geo<T, N>;
+  unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
+  const T s = S[si];
+  if (s < tinf<T>()) {
+    const int i = si % N, j = (si / N) % N, k = si / (N * N);
+    const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+    const T v = U[t];
+    const T nv = local_solve(nmin(U[t - 1], U[t + 1]), nmin(U[t - G::SY], U[t + G::SY]),
+                             nmin(U[t - G::SZ], U[t + G::SZ]), s);
+    ++n_updates;
+    if (vlt(nv, v)) {
+      U[t] = nv;
+      c1 |= drop_exceeds(nv, v, (float)kappa) ? (kWritten | kBig | kStep) : kWritten;
+    }
   }
+  chg[si] = c1;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void wake_users(const T* __restrict__ U, unsigned* __restrict__ chg,
+                                           int si) {
+  using G = Geo<T, N>;
+  atomicAnd(chg + si, ~kStep);
+  const int i = si % N, j = (si / N) % N, k = si / (N * N);
+  const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+  const T nv = U[t];
+  auto consider = [&](bool inside, int ny, int ty, int tf) {
+    if (inside && !(chg[ny] & kActive) && vlt(nv, U[ty]) && vlt(nv, U[tf]))
+      atomicOr(chg + ny, kActive);
+  };
+  consider(i > 0, si - 1, t - 1, t - 2);
+  consider(i < N - 1, si + 1, t + 1, t + 2);
+  consider(j > 0, si - N, t - G::SY, t - 2 * G::SY);
+  consider(j < N - 1, si + N, t + G::SY, t + 2 * G::SY);
+  consider(k > 0, si - N * N, t - G::SZ, t - 2 * G::SZ);
+  consider(k < N - 1, si + N * N, t + G::SZ, t + 2 * G::SZ);
 }
 
 // One pass over a cell's nodes in the level order of its table (see
 // polish_levels_kernel): level by level, the active nodes of a level
 // together.  A node's FP32 upwind neighbours have smaller levels, so where
 // the FP64 values keep the FP32 order one pass settles the cell; a node
-// whose FP64 inflow comes from a later node is left active for the sweeps
-// that follow.  Table entries are read from global memory, the next
-// level's while the current one runs.
+// whose FP64 inflow comes from a later node is left active.  Each chunk of a
+// level (UNR nodes a thread) runs in two steps split by a barrier: every
+// node first takes its new value, and only then are the neighbours that can
+// use a new value woken, comparing with their settled values (without the
+// split a node would compare with a same-level neighbour still at its
+// lifted start value and wake it for nothing).  perm and loff are the
+// staged table (node indices, level starts).
 template <typename T, int N, int WPC>
 __device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restrict__ S,
                                            unsigned* __restrict__ chg,
@@ -219,40 +261,23 @@ __device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restric
                                            int tid, int worker, T kappa, unsigned& n_updates) {
   constexpr int NT = WPC * 32;
   constexpr int UNR = 2;
-  constexpr unsigned kNone = 0xffffu;
-  unsigned left = 0;
-  int lo = loff[0], hi = loff[1];
-  unsigned nxt[UNR];
-#pragma unroll
-  for (int h = 0; h < UNR; ++h) {
-    const int e = lo + tid + h * NT;
-    nxt[h] = e < hi ? (unsigned)perm[e] : kNone;
-  }
   for (int l = 0; l < depth; ++l) {
-    unsigned cur[UNR];
-#pragma unroll
-    for (int h = 0; h < UNR; ++h) cur[h] = nxt[h];
-    const int clo = lo, chi = hi;
-    if (l + 1 < depth) {
-      lo = hi;
-      hi = loff[l + 2];
+    const int lo = loff[l], hi = loff[l + 1];
+    for (int c0 = lo; c0 < hi; c0 += UNR * NT) {
+      int mine[UNR];
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {
-        const int e = lo + tid + h * NT;
-        nxt[h] = e < hi ? (unsigned)perm[e] : kNone;
+        const int e = c0 + tid + h * NT;
+        mine[h] = e < hi ? (int)perm[e] : -1;
+        if (mine[h] >= 0 && (chg[mine[h]] & kActive))
+          take_node<T, N>(U, S, chg, mine[h], kappa, n_updates);
       }
-    }
+      worker_sync<WPC>(worker);
 #pragma unroll
-    for (int h = 0; h < UNR; ++h)
-      if (cur[h] != kNone && (chg[cur[h] & (unsigned)(N * N * N - 1)] & kActive))
-        update_node<T, N, false, true>(U, S, chg, (int)cur[h], 0, 0, 0, kappa, n_updates, left);
-    // a level larger than the prefetched slots
-    for (int e = clo + tid + UNR * NT; e < chi; e += NT) {
-      const int si = perm[e];
-      if (chg[si] & kActive)
-        update_node<T, N, false, true>(U, S, chg, si, 0, 0, 0, kappa, n_updates, left);
+      for (int h = 0; h < UNR; ++h)
+        if (mine[h] >= 0 && (chg[mine[h]] & kStep)) wake_users<T, N>(U, chg, mine[h]);
+      worker_sync<WPC>(worker);
     }
-    worker_sync<WPC>(worker);
   }
 }
 
@@ -515,13 +540,24 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     const T kappa = (T)(p.kappa_from_ctl ? ctl->kappa_bulk : I.kappa);
 
     // ---- 2. stage cell + halo ------------------------------------------
+    // (and, for the level pass of the polish, the cell's level table)
+    int lev_depth = 0;
+    if constexpr (!REPLACE && sizeof(T) == 8)
+      if (p.use_levels) lev_depth = cells.lev_depth[cell];
     fence_proxy_async_smem();
     worker_sync<WPC>(worker);
     if (tid == 0) {
       fence_proxy_async_global();
-      mbar_arrive_expect_tx(bar, (unsigned)(G::UBYTES + G::SBYTES));
+      const unsigned lev_bytes = lev_depth > 0 ? (unsigned)(G::N3 * 2 + (kMaxLevels + 1) * 2) : 0u;
+      mbar_arrive_expect_tx(bar, (unsigned)(G::UBYTES + G::SBYTES) + lev_bytes);
       tma_load_3d(U, p.tmaps + ii, N * cx, N * cy, N * cz, bar);
       bulk_load(S, static_cast<const T*>(I.s) + (size_t)lc * G::N3, (unsigned)G::SBYTES, bar);
+      if (lev_bytes) {
+        bulk_load(wbase + G::OFF_PERM, cells.lev_perm + (size_t)cell * G::N3,
+                  (unsigned)(G::N3 * 2), bar);
+        bulk_load(wbase + G::OFF_LOFF, cells.lev_off + (size_t)cell * (kMaxLevels + 1),
+                  (unsigned)((kMaxLevels + 1) * 2), bar);
+      }
     }
     // On a first visit every node starts active.  After a converged visit
     // only the halo can have changed (a cell's nodes have one writer, the
@@ -581,15 +617,13 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     if constexpr (!REPLACE && sizeof(T) == 8) {
       // polish: one pass in the level order read off the FP32 result first;
       // the sweeps below only pick up what it left active
-      if (p.use_levels) {
-        const int depth = cells.lev_depth[cell];
-        if (depth > 0) {
-          level_pass<T, N, WPC>(U, S, chg, cells.lev_perm + (size_t)cell * G::N3,
-                                cells.lev_off + (size_t)cell * (kMaxLevels + 1), depth, tid,
-                                worker, kappa, n_updates);
-          ++nsw;
-          all_active = false;
-        }
+      if (lev_depth > 0) {
+        level_pass<T, N, WPC>(U, S, chg,
+                              reinterpret_cast<const unsigned short*>(wbase + G::OFF_PERM),
+                              reinterpret_cast<const unsigned short*>(wbase + G::OFF_LOFF),
+                              lev_depth, tid, worker, kappa, n_updates);
+        ++nsw;
+        all_active = false;
       }
     }
     auto run = [&](int d) {

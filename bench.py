@@ -494,6 +494,49 @@ def run_ours(args):
             "sweeps": std["sweeps"],
             "max_rel_err_vs_oracle": (float(np.max(np.abs(ud.cpu().numpy() - ref)) / np.max(ref))
                                       if cpu is not None else None)}
+        # the other named workloads: 65^3 point source (FP64, 8^3 cells) and
+        # the 513^3 barrier field (FP32 + FP64 polish; checked by the oracle's
+        # residual at every node, a full FMM of 135 M nodes being too slow here)
+        p1 = W.point_source_const(65)
+        d1 = [torch.from_numpy(x).to(dev) for x in (p1.F, p1.mask, p1.q)]
+        u1 = torch.empty(p1.F.shape, dtype=torch.float64, device=dev)
+        with eik.Solver(precision="fp64", cell_n=8, device=local) as s1:
+            s1.solve(d1[0], d1[1], d1[2], p1.h, tol=args.tol, out=u1)
+            ts = []
+            for _ in range(5):
+                flush.fill_(1.0)
+                _, st = s1.solve(d1[0], d1[1], d1[2], p1.h, tol=args.tol, out=u1)
+                ts.append(st["seconds"])
+        r1 = None
+        if cpu is not None:
+            import oracle
+            f1 = oracle.fmm(p1.F, p1.mask, p1.q, p1.h)
+            r1 = float(np.max(np.abs(u1.cpu().numpy() - f1)) / np.max(f1))
+        extras["point_source_65_fp64"] = {
+            "nodes": p1.nodes, "nodes_per_s": p1.nodes / statistics.mean(ts),
+            "ms": statistics.mean(ts) * 1e3, "cell_n": 8, "max_rel_err_vs_oracle": r1}
+        del d1, u1
+        p3 = W.barrier_blocks(513)
+        d3 = [torch.from_numpy(x).to(dev) for x in (p3.F, p3.mask, p3.q)]
+        u3 = torch.empty(p3.F.shape, dtype=torch.float64, device=dev)
+        with eik.Solver(precision="fp32_polish", device=local) as s3:
+            s3.solve(d3[0], d3[1], d3[2], p3.h, tol=args.tol, out=u3)
+            ts = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                _, st3 = s3.solve(d3[0], d3[1], d3[2], p3.h, tol=args.tol, out=u3)
+                ts.append(st3["seconds"])
+        res3 = None
+        if cpu is not None:
+            import oracle
+            rr, bad = oracle.residual(u3.cpu().numpy(), p3.F, p3.mask, p3.h)
+            res3 = {"max_abs_residual": rr, "nonfinite": bad,
+                    "rel_to_max_u": rr / float(st3["u_max"])}
+        extras["barrier_513_fp32_polish"] = {
+            "nodes": p3.nodes, "nodes_per_s": p3.nodes / statistics.mean(ts),
+            "ms": statistics.mean(ts) * 1e3, "cell_n": st3["cell_n_used"],
+            "fallback_used": st3["fallback_used"], "oracle_residual": res3}
+        del d3, u3
         extras["serving"] = run_serving(eik, W, local, args.serve_requests,
                                         args.serve_unique, tol=args.tol,
                                         check=cpu is not None)
@@ -513,7 +556,10 @@ def run_ours(args):
                    "l2": "256 MB L2 flush between steps (outside the step events); the "
                          "solve's working set (~0.6 GB) also exceeds the 129 MB L2"},
         "e2e": {"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "host_io": "page-locked host buffers: F read in place, q read in place at "
+                           "exit nodes only, mask copied, u written in place by the final "
+                           "kernel; the byte counts are those of the caller's arrays"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -526,12 +572,6 @@ def run_ours(args):
         "fallback_used": int(sum(s["fallback_used"] for s in stats)),
         "visits": {"bulk": vb, "polish": vp, "cells": int(math.ceil(args.edge / n) ** 3)},
         "max_rel_err_vs_oracle": err_rel,
-        # FP64 pipe view of the polish: ~14 FP64-pipe instructions per local
-        # solve (Newton-refined form), against 1.25 TFLOP/s / 2 = 0.625 T
-        # FP64 instructions/s nominal
-        "fp64_pipe_estimate": ({"instr_per_s": 14 * statistics.mean(
-            s["polish_node_updates"] for s in stats) / tp, "peak_instr_per_s": 0.625e12}
-            if tp else None),
         "residual_max": last["residual_max"],
         "bulk_ms": tb * 1e3, "polish_ms": tp * 1e3,
         "wall_s_timed_region": wall,

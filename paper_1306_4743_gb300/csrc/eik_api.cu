@@ -308,6 +308,20 @@ bool valid_dims(const int64_t* d) {
   return nodes <= (1ll << 34);
 }
 
+// The device address of a page-locked host buffer (cudaHostAlloc or
+// cudaHostRegister), else nullptr.  Kernels read such a buffer in place
+// over the CPU-GPU link, so the solve need not copy what it only samples
+// (q, read at exit nodes only) or reads once (F); the result can be written
+// straight into it.  Pageable memory is always copied.
+const void* pinned_alias(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 }  // namespace
 
 // Launch sequence of one batched solve.  IO arrays are host pointers when
@@ -350,6 +364,19 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   Lr.async_out = async_out && host_io;
   Lr.nodes_total = nodes_total;
   Lr.outs.assign(u_out, u_out + count);
+  // page-locked host inputs are read in place, and a page-locked output of
+  // a synchronous call is written in place (an asynchronous one keeps its
+  // staging buffer, as its caller may cancel and free it)
+  std::vector<const float*> Fd(count, nullptr);
+  std::vector<const double*> Qd(count, nullptr);
+  std::vector<double*> Od(count, nullptr);
+  if (host_io) {
+    for (int t = 0; t < count; ++t) {
+      Fd[t] = static_cast<const float*>(pinned_alias(F[t]));
+      Qd[t] = static_cast<const double*>(pinned_alias(q[t]));
+      if (!async_out) Od[t] = static_cast<double*>(const_cast<void*>(pinned_alias(u_out[t])));
+    }
+  }
   if (Lr.async_out) {
     size_t ob = 0;
     for (int t = 0; t < count; ++t) {
@@ -406,9 +433,9 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
       if (rc) return rc;
     }
     PrepInstance& P = hp[t];
-    P.F = host_io ? reinterpret_cast<const float*>(A + I.off_F) : F[t];
+    P.F = host_io ? (Fd[t] ? Fd[t] : reinterpret_cast<const float*>(A + I.off_F)) : F[t];
     P.mask = host_io ? reinterpret_cast<const uint8_t*>(A + I.off_mask) : mask[t];
-    P.q = host_io ? reinterpret_cast<const double*>(A + I.off_q) : q[t];
+    P.q = host_io ? (Qd[t] ? Qd[t] : reinterpret_cast<const double*>(A + I.off_q)) : q[t];
     P.h = I.h;
     P.u = b.u;
     P.s = A + I.off_sb;
@@ -449,7 +476,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     Fi.q = P.q;
     Fi.u64 = A + I.off_u64;
     Fi.s64 = A + I.off_s64;
-    Fi.out = host_io ? reinterpret_cast<double*>(A + I.off_out) : u_out[t];
+    Fi.out = host_io ? (Od[t] ? Od[t] : reinterpret_cast<double*>(A + I.off_out)) : u_out[t];
     Fi.px64 = I.px64;
     Fi.py = I.py;
     Fi.pz = I.pz;
@@ -472,9 +499,11 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   if (host_io) {
     for (int t = 0; t < count; ++t) {
       const InstPlan& I = L.inst[t];
-      CK(cudaMemcpyAsync(A + I.off_F, F[t], (size_t)I.nodes * 4, cudaMemcpyHostToDevice, st));
+      if (!Fd[t])
+        CK(cudaMemcpyAsync(A + I.off_F, F[t], (size_t)I.nodes * 4, cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(A + I.off_mask, mask[t], (size_t)I.nodes, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(A + I.off_q, q[t], (size_t)I.nodes * 8, cudaMemcpyHostToDevice, st));
+      if (!Qd[t])
+        CK(cudaMemcpyAsync(A + I.off_q, q[t], (size_t)I.nodes * 8, cudaMemcpyHostToDevice, st));
     }
   }
   CK(cudaMemcpyAsync(A + L.small_begin, hs, L.small_end - L.small_begin, cudaMemcpyHostToDevice,
@@ -557,6 +586,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   CK(cudaMemcpyAsync(hres, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   if (host_io) {
     for (int t = 0; t < count; ++t) {
+      if (Od[t]) continue;  // written in place by the final kernel
       const InstPlan& I = L.inst[t];
       void* dst = Lr.async_out ? (void*)(ex.h_out + Lr.out_off[t]) : (void*)u_out[t];
       CK(cudaMemcpyAsync(dst, A + I.off_out, (size_t)I.nodes * 8, cudaMemcpyDeviceToHost, st));

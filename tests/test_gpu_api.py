@@ -55,6 +55,22 @@ def test_device_buffers_match_host_buffers(eik, torch, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
+def test_pinned_host_buffers_are_used_in_place(eik, torch, precision):
+    # page-locked F and q are read in place and a page-locked u is written in
+    # place; the result equals the one from pageable buffers (copied)
+    p = W.gaussian_bumps((45, 38, 29), seed=21)
+    F, m, q = (torch.from_numpy(a).pin_memory() for a in (p.F, p.mask, p.q))
+    out = torch.full(p.F.shape, -1.0, dtype=torch.float64).pin_memory()
+    with eik.Solver(precision=precision, cell_n=8) as s:
+        s.solve(F.numpy(), m.numpy(), q.numpy(), p.h, out=out.numpy())
+        u_pageable, _ = s.solve(p.F, p.mask, p.q, p.h)
+    u = out.numpy()
+    assert rel_err(u, p) <= TOL[precision]
+    assert np.array_equal(u[p.mask == 1], p.q[p.mask == 1])
+    assert np.max(np.abs(u - u_pageable)) <= TOL[precision] * np.max(np.abs(u_pageable))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
 def test_batch_matches_single_solves(eik, precision):
     probs = [W.gaussian_bumps(d, 4000 + k) for k, d in
              enumerate([(33, 65, 33), (65, 33, 33), (33, 33, 33), (41, 27, 19), (9, 9, 9)])]

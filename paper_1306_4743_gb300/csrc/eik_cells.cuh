@@ -44,9 +44,6 @@ __device__ __forceinline__ bool vlt(double a, double b) { return dlt_nn(a, b); }
 // the latency of word accesses, and these bits sit on the sweep's
 // critical path.
 constexpr unsigned kWritten = 1, kBig = 2, kActive = 4;
-// level pass of the polish: changed above kappa in the current step,
-// neighbours still to be activated
-constexpr unsigned kStep = 8;
 
 template <typename T, int N>
 struct Geo {
@@ -126,7 +123,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
   const T s = S[si];
   unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
   auto activate = [&](int nb) { chg[nb] |= kActive; };
-  if (s < tinf<T>()) {
+  if (vlt(s, tinf<T>())) {
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
     const T v = U[t];
     const T xm = U[t - 1], xp = U[t + 1];
@@ -193,19 +190,22 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
 
 // Level-pass helpers (min mode, Alg. 2).  take_node: node si is active and
 // no other thread writes its flag word in this step: clear its active bit,
-// recompute it from its six neighbours (Eq. 2), store a lower value and
-// mark a change above kappa with kStep.  wake_users: for a node marked
-// kStep, clear the mark and activate the neighbours that may now use its
-// value (below the neighbour and below the neighbour's other neighbour on
-// that axis); a neighbour that is still active is left alone.
+// recompute it from its six neighbours (Eq. 2), store a lower value, and
+// return whether it changed by more than kappa.  wake_users: activate the
+// neighbours of si that may now use its value (below the neighbour and
+// below the neighbour's other neighbour on that axis); a neighbour that is
+// still active is left alone.  In the wake step no thread writes a flag
+// word except to set kActive, so concurrent activations of one neighbour
+// all store the same word and need no atomics.
 template <typename T, int N>
-__device__ __forceinline__ void take_node(T* __restrict__ U, const T* __restrict__ S,
+__device__ __forceinline__ bool take_node(T* __restrict__ U, const T* __restrict__ S,
                                           unsigned* __restrict__ chg, int si, T kappa,
                                           unsigned& n_updates) {
   using G = Geo<T, N>;
   unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
   const T s = S[si];
-  if (s < tinf<T>()) {
+  bool big = false;
+  if (vlt(s, tinf<T>())) {
     const int i = si % N, j = (si / N) % N, k = si / (N * N);
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
     const T v = U[t];
@@ -214,23 +214,26 @@ __device__ __forceinline__ void take_node(T* __restrict__ U, const T* __restrict
     ++n_updates;
     if (vlt(nv, v)) {
       U[t] = nv;
-      c1 |= drop_exceeds(nv, v, (float)kappa) ? (kWritten | kBig | kStep) : kWritten;
+      big = drop_exceeds(nv, v, (float)kappa);
+      c1 |= big ? (kWritten | kBig) : kWritten;
     }
   }
   chg[si] = c1;
+  return big;
 }
 
 template <typename T, int N>
 __device__ __forceinline__ void wake_users(const T* __restrict__ U, unsigned* __restrict__ chg,
                                            int si) {
   using G = Geo<T, N>;
-  atomicAnd(chg + si, ~kStep);
   const int i = si % N, j = (si / N) % N, k = si / (N * N);
   const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
   const T nv = U[t];
   auto consider = [&](bool inside, int ny, int ty, int tf) {
-    if (inside && !(chg[ny] & kActive) && vlt(nv, U[ty]) && vlt(nv, U[tf]))
-      atomicOr(chg + ny, kActive);
+    if (inside) {
+      const unsigned w = chg[ny];
+      if (!(w & kActive) && vlt(nv, U[ty]) && vlt(nv, U[tf])) chg[ny] = w | kActive;
+    }
   };
   consider(i > 0, si - 1, t - 1, t - 2);
   consider(i < N - 1, si + 1, t + 1, t + 2);
@@ -262,18 +265,19 @@ __device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restric
   for (int l = 0; l < depth; ++l) {
     const int lo = loff[l], hi = loff[l + 1];
     for (int c0 = lo; c0 < hi; c0 += UNR * NT) {
-      int mine[UNR];
+      int mine[UNR];  // node taken with a change above kappa, else -1
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {
         const int e = c0 + tid + h * NT;
-        mine[h] = e < hi ? (int)perm[e] : -1;
-        if (mine[h] >= 0 && (chg[mine[h]] & kActive))
-          take_node<T, N>(U, S, chg, mine[h], kappa, n_updates);
+        const int si = e < hi ? (int)perm[e] : -1;
+        mine[h] = -1;
+        if (si >= 0 && (chg[si] & kActive) && take_node<T, N>(U, S, chg, si, kappa, n_updates))
+          mine[h] = si;
       }
       worker_sync<WPC>(worker);
 #pragma unroll
       for (int h = 0; h < UNR; ++h)
-        if (mine[h] >= 0 && (chg[mine[h]] & kStep)) wake_users<T, N>(U, chg, mine[h]);
+        if (mine[h] >= 0) wake_users<T, N>(U, chg, mine[h]);
       worker_sync<WPC>(worker);
     }
   }

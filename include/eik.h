@@ -184,6 +184,10 @@ int eik_struct_sizes(size_t *opts_bytes, size_t *stats_bytes);
  *              changes).  Applies to the FP64 sweeps of either precision mode.
  *   u_out    = caller-owned nx*ny*nz doubles, written on EIK_OK
  *   stats    = may be NULL
+ * Host buffers that are page-locked (cudaHostAlloc / cudaHostRegister) are
+ * used in place: the device reads F and q (q only at exit nodes) and writes
+ * u_out over the CPU-GPU link instead of the call copying them; pageable
+ * buffers are copied.  Either way the call returns with u_out written.
  * Returns EIK_OK or an error code; on error u_out is unspecified.
  */
 int eik_solve(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
@@ -252,7 +256,11 @@ int eik_solve_batch_device(eik_ctx *ctx, int count, const int64_t *dims,
  * requests) and sets *done = 1 once the ticket's u_out is written; it then
  * returns the ticket's status, and the ticket is forgotten.  eik_cancel
  * drops a ticket that has not completed; a batch already on the device
- * finishes into a private buffer.  Unknown tickets give EIK_ENOTFOUND.
+ * finishes into a private buffer, except that a page-locked u_out
+ * (cudaHostAlloc / cudaHostRegister) is written in place by the device, so
+ * eik_cancel of such a request on the device first waits for its batch to
+ * finish.  Page-locked F and q are read in place (no copy), as in
+ * eik_solve.  Unknown tickets give EIK_ENOTFOUND.
  */
 int eik_submit(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
                const uint8_t *src_mask, const double *q, double tol,

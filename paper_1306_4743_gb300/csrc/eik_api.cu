@@ -335,9 +335,9 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   Lr.async_out = async_out && host_io;
   Lr.nodes_total = nodes_total;
   Lr.outs.assign(u_out, u_out + count);
-  // page-locked host inputs are read in place, and a page-locked output of
-  // a synchronous call is written in place (an asynchronous one keeps its
-  // staging buffer, as its caller may cancel and free it)
+  // page-locked host inputs are read in place, and a page-locked output is
+  // written in place by the final kernel (eik_cancel of such a request on
+  // the device waits for its batch)
   std::vector<const float*> Fd(count, nullptr);
   std::vector<const double*> Qd(count, nullptr);
   std::vector<double*> Od(count, nullptr);
@@ -345,18 +345,22 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     for (int t = 0; t < count; ++t) {
       Fd[t] = static_cast<const float*>(pinned_alias(F[t]));
       Qd[t] = static_cast<const double*>(pinned_alias(q[t]));
-      if (!async_out) Od[t] = static_cast<double*>(const_cast<void*>(pinned_alias(u_out[t])));
+      Od[t] = static_cast<double*>(const_cast<void*>(pinned_alias(u_out[t])));
     }
   }
+  Lr.direct.assign(count, 0);
+  for (int t = 0; t < count; ++t) Lr.direct[t] = Od[t] ? 1 : 0;
   if (Lr.async_out) {
     size_t ob = 0;
     for (int t = 0; t < count; ++t) {
       Lr.out_off.push_back(ob);
       Lr.out_nodes.push_back(L.inst[t].nodes);
-      ob += align_up((size_t)L.inst[t].nodes * 8, 256);
+      if (!Od[t]) ob += align_up((size_t)L.inst[t].nodes * 8, 256);
     }
-    rc = ensure_pinned(&ex.h_out, &ex.h_out_size, ob);
-    if (rc) return rc;
+    if (ob) {
+      rc = ensure_pinned(&ex.h_out, &ex.h_out_size, ob);
+      if (rc) return rc;
+    }
   }
   char* A = ex.arena;
 
@@ -575,7 +579,8 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
   const long long nodes_total = Lr.nodes_total;
   if (Lr.async_out) {
     for (int t = 0; t < Lr.count; ++t)
-      memcpy(Lr.outs[t], ex.h_out + Lr.out_off[t], (size_t)Lr.out_nodes[t] * 8);
+      if (!Lr.direct[t])
+        memcpy(Lr.outs[t], ex.h_out + Lr.out_off[t], (size_t)Lr.out_nodes[t] * 8);
   }
   if (stats) {
     memset(stats, 0, sizeof(*stats));

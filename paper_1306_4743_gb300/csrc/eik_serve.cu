@@ -277,12 +277,17 @@ int eik_cancel(eik_ctx* ctx, uint64_t ticket) {
   Request* r = it->second;
   if (r->state == 1) {
     // on the device: let the batch finish, but write its result into a
-    // private sink so the caller may free u_out now
+    // private sink so the caller may free u_out now; a result written in
+    // place (page-locked u_out) cannot be redirected, so wait for the batch
     const size_t nodes = (size_t)r->dims[0] * r->dims[1] * r->dims[2];
     for (Slot& sl : s->slots) {
       if (!sl.busy) continue;
       for (int t = 0; t < (int)sl.tickets.size(); ++t) {
         if (sl.tickets[t] != ticket) continue;
+        if (sl.L.direct[t]) {
+          cudaStreamSynchronize(sl.ex.stream);
+          continue;
+        }
         double* sink = new (std::nothrow) double[nodes];
         if (!sink) return EIK_ENOMEM;
         sl.L.outs[t] = sink;  // the finish copies here; freed on retire

@@ -43,6 +43,7 @@ struct Launch {
   std::vector<double*> outs;
   std::vector<size_t> out_off;  // offsets in h_out (asynchronous host outputs)
   std::vector<long long> out_nodes;
+  std::vector<char> direct;     // 1: the result is written in place (page-locked u_out)
 };
 
 int exec_init(Exec& e, bool own_stream);

@@ -85,6 +85,27 @@ def test_budget_limits_admission_but_everything_finishes(eik):
         assert rc == 3  # EIK_EBUDGET
 
 
+def test_pinned_buffers_in_place_and_cancel_waits(eik):
+    # page-locked inputs are read in place and page-locked outputs written in
+    # place; cancelling such a request on the device waits for its batch
+    torch = pytest.importorskip("torch")
+    probs = _requests()[:6]
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    ins = [(pin(p.F), pin(p.mask), pin(p.q)) for p in probs]
+    outs = [torch.full(p.F.shape, -1.0, dtype=torch.float64).pin_memory() for p in probs]
+    with eik.Solver(precision="fp32_polish") as s:
+        tickets = [s.submit(F.numpy(), m.numpy(), q.numpy(), p.h, out=o.numpy())[0]
+                   for (F, m, q), o, p in zip(ins, outs, probs)]
+        assert s.cancel(tickets[0]) == 0  # likely on the device: returns after its batch
+        done = _drain(s, tickets[1:])
+        assert all(v[0] == 0 for v in done.values())
+    for o, p in zip(outs[1:], probs[1:]):
+        u = o.numpy()
+        ref = oracle.fmm(p.F, p.mask, p.q, p.h)
+        assert np.max(np.abs(u - ref)) <= TOL * np.max(ref)
+        assert np.array_equal(u[p.mask == 1], p.q[p.mask == 1])
+
+
 def test_cancel_waiting_and_running(eik):
     probs = _requests()[:5]
     with eik.Solver(precision="fp32_polish") as s:

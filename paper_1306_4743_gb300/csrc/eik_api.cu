@@ -54,6 +54,9 @@ struct eik_ctx {
   // execution slot of the captured device-batch graph (its staging is only
   // written while capturing, so a replay uploads the captured tables)
   Exec gexec;
+  // plane tables, per cell size (index 0: n=4, 1: n=8, 2: n=16)
+  unsigned short* d_tab[3] = {nullptr, nullptr, nullptr};
+  int* d_off[3] = {nullptr, nullptr, nullptr};
   // serving
   ServeState* serve = nullptr;
   // autotune results: log2(nodes) bucket -> (cell size, CTAs of the cell kernel)
@@ -63,6 +66,31 @@ struct eik_ctx {
 namespace {
 
 int size_index(int n) { return n == 4 ? 0 : n == 8 ? 1 : n == 16 ? 2 : -1; }
+
+cudaError_t ensure_plane_table(eik_ctx* ctx, int n) {
+  const int si = size_index(n);
+  if (ctx->d_tab[si]) return cudaSuccess;
+  const int n3 = n * n * n, np = 3 * (n - 1) + 1;
+  std::vector<unsigned short> tab;
+  std::vector<int> off(np + 1, 0);
+  tab.reserve(n3);
+  for (int C = 0; C < np; ++C) {
+    off[C] = (int)tab.size();
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b) {
+        const int a = C - b - c;
+        if (a >= 0 && a < n) tab.push_back((unsigned short)(a + n * (b + n * c)));
+      }
+  }
+  off[np] = (int)tab.size();
+  cudaError_t e = cudaMalloc(&ctx->d_tab[si], n3 * sizeof(unsigned short));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&ctx->d_off[si], (np + 1) * sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(ctx->d_tab[si], tab.data(), n3 * sizeof(unsigned short), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(ctx->d_off[si], off.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice);
+}
 
 // Layout of one instance inside a launch.
 struct InstPlan {
@@ -317,6 +345,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   const int n = n_override ? n_override : choose_cell_n(ctx, nodes_max);
   if (size_index(n) < 0) return EIK_EINVAL;
   CK(cudaSetDevice(ctx->device));
+  CK(ensure_plane_table(ctx, n));
 
   LaunchPlan L;
   make_plan(L, count, dims, h, n, polish, host_io);
@@ -512,6 +541,8 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap_b);
   p.cells = cells;
   p.ctl = dctl;
+  p.plane_tab = ctx->d_tab[size_index(n)];
+  p.plane_off = ctx->d_off[size_index(n)];
   p.spin_cap_ns = ctx->opts.spin_cap_us * 1000ull;
   p.max_sweeps = ctx->opts.max_sweeps_per_visit;
   p.pass = 0;
@@ -814,6 +845,10 @@ int eik_destroy(eik_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   exec_free(c->main);
   exec_free(c->gexec);
+  for (int i = 0; i < 3; ++i) {
+    if (c->d_tab[i]) cudaFree(c->d_tab[i]);
+    if (c->d_off[i]) cudaFree(c->d_off[i]);
+  }
   if (c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

@@ -86,8 +86,10 @@ struct Geo {
   static constexpr int OFF_LOFF = OFF_PERM + PERM_BYTES;
   static constexpr int OFF_BAR = OFF_LOFF + LOFF_BYTES;
   static constexpr int WORKER_BYTES = OFF_BAR + 128;
-  // CTA-wide head (nothing at present)
-  static constexpr int HEAD_BYTES = 0;
+  // CTA-wide: plane table | plane offsets
+  static constexpr int TAB_BYTES = align128(N3 * 2);
+  static constexpr int OFFS_BYTES = align128((NPLANES + 1) * 4);
+  static constexpr int HEAD_BYTES = TAB_BYTES + OFFS_BYTES;
 };
 
 template <int WPC>
@@ -356,35 +358,11 @@ __device__ __forceinline__ void active_planes(const unsigned* __restrict__ chg, 
 // the warp issues a node's arithmetic only for nodes that need it.  This
 // matters for FP64, whose narrow pipe costs the same per warp instruction
 // however few lanes are active.
-// Which node of a plane a worker slot takes, without a table.  The cell's
-// nodes lie on n^2 pencils along x, (b, c) fixed; pencil (b, c) crosses
-// plane C (in the sweep's reflected coordinates) at a = C - b - c.  Slot s
-// owns up to two pencils that never cross the same plane: one with b + c = d
-// (base1 = n b + n^2 c) and one with b + c = d + n (base2), d in [0, n).
-// Grouped by d, the slots number exactly the most nodes on one plane
-// (12, 48, 192 for n = 4, 8, 16), so every plane fits one pass of the worker.
-template <int N>
-__device__ __forceinline__ void plane_slot(int s, int& d, int& base1, int& base2) {
-  d = -1;
-  base1 = -1;
-  base2 = -1;
-  int start = 0;
-#pragma unroll
-  for (int dd = 0; dd < N; ++dd) {
-    const int g = dd == N - 1 ? N : (dd + 1 > N - 1 - dd ? dd + 1 : N - 1 - dd);
-    if (d < 0 && s < start + g) {
-      const int k = s - start;
-      d = dd;
-      if (k < dd + 1) base1 = N * k + N * N * (dd - k);                      // b = k
-      if (dd < N - 1 && k < N - 1 - dd) base2 = N * (dd + 1 + k) + N * N * (N - 1 - k);  // c = n-1-k
-    }
-    start += g;
-  }
-}
-
 template <typename T, int N, int WPC, bool REPLACE, bool COMPACT>
 __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __restrict__ S,
                                                unsigned* __restrict__ chg,
+                                               const unsigned short* __restrict__ tab,
+                                               const int* __restrict__ off,
                                                unsigned short* __restrict__ list, int dir,
                                                int first, int last, int tid, int worker,
                                                T kappa, unsigned& n_updates) {
@@ -400,23 +378,24 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
   const int fx = (dir & 1) ? N - 1 : 0;
   const int fy = (dir & 2) ? N - 1 : 0;
   const int fz = (dir & 4) ? N - 1 : 0;
-  // n is a power of two, so reflecting i, j, k for direction `dir` is one XOR
+  // n is a power of two, so the index of a node in the order of direction
+  // `dir` is the table's index with i, j, k reflected: one XOR
   const unsigned dmask = (unsigned)(fx + N * (fy + N * fz));
-  int sd[UNR], sb1[UNR], sb2[UNR];
-#pragma unroll
-  for (int h = 0; h < UNR; ++h) plane_slot<N>(tid + h * NT, sd[h], sb1[h], sb2[h]);
+  // A plane's nodes are packed into the lowest slots (a small plane keeps
+  // few warps busy, which matters for FP64 whose pipe is paid per warp
+  // instruction).  Loading the plane's entries at its start measured
+  // faster than loading them two planes ahead: a barrier waits for loads
+  // still in flight.
   unsigned left = 0;
   for (int C = first; C < G::NPLANES; ++C) {
     unsigned cur[UNR];
+    {
+      const int b0 = off[C], e1 = off[C + 1];
 #pragma unroll
-    for (int h = 0; h < UNR; ++h) {
-      const int a = C - sd[h];
-      int node = -1;
-      if (sd[h] >= 0) {
-        if (a >= 0 && a < N) node = sb1[h] >= 0 ? a + sb1[h] : -1;
-        else if (a >= N && a < 2 * N) node = sb2[h] >= 0 ? a - N + sb2[h] : -1;
+      for (int h = 0; h < UNR; ++h) {
+        const int e = b0 + tid + h * NT;
+        cur[h] = e < e1 ? ((unsigned)tab[e] ^ dmask) : kNone;
       }
-      cur[h] = node >= 0 ? ((unsigned)node ^ dmask) : kNone;
     }
     // the active bits of all of this thread's nodes first (Alg. 2 l.1-2),
     // so that their loads overlap
@@ -472,6 +451,11 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   // Nothing queued (the replace-mode fallback after a passing check, or all
   // work already done): leave at once, as one block.
   if (__syncthreads_and(ld_acquire_s32(&p.ctl->active) <= 0)) return;
+  unsigned short* tab = reinterpret_cast<unsigned short*>(smem);
+  int* off = reinterpret_cast<int*>(smem + G::TAB_BYTES);
+  for (int e = threadIdx.x; e < G::N3; e += blockDim.x) tab[e] = p.plane_tab[e];
+  for (int e = threadIdx.x; e <= G::NPLANES; e += blockDim.x) off[e] = p.plane_off[e];
+
   const int worker = threadIdx.x / NT;
   const int tid = threadIdx.x % NT;
   const int lane = tid & 31;
@@ -640,7 +624,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
         lm = 0;  // nothing active: converged without a sweep
         return;
       }
-      lm = sweep_cell<T, N, WPC, REPLACE, COMPACT>(U, S, chg, list, d, first, last, tid,
+      lm = sweep_cell<T, N, WPC, REPLACE, COMPACT>(U, S, chg, tab, off, list, d, first, last, tid,
                                                    worker, kappa, n_updates);
       ++nsw;
     };

@@ -127,6 +127,8 @@ struct CellKernelParams {
   const CUtensorMap* tmaps;      // one per instance, 64-byte aligned
   CellArrays cells;
   Control* ctl;
+  const unsigned short* plane_tab;  // in-cell node index a + n (b + n c), by plane
+  const int* plane_off;             // plane start offsets, 3(n-1)+2 entries
   unsigned long long spin_cap_ns;
   int max_sweeps;
   int pass;                         // counter set: 0 bulk, 1 polish, 2 fallback

@@ -111,7 +111,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   for (int a = 0; a < 3; ++a)
     if (dims[a] < 1 || dims[a] > (1 << 24)) return EIK_EINVAL;
   if (!(h > 0.0) || isinf(h) || !(tol >= 0.0) || isinf(tol)) return EIK_EINVAL;
-  const int n = kNoallocCellN, n3 = n * n * n;
+  const int n = kNoallocCellN, n3 = n * n * n, np = 3 * (n - 1) + 1;
   const int nx = (int)dims[0], ny = (int)dims[1], nz = (int)dims[2];
   const int ncx = (nx + n - 1) / n, ncy = (ny + n - 1) / n, ncz = (nz + n - 1) / n;
   const long long ncells = (long long)ncx * ncy * ncz;
@@ -142,6 +142,8 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   const size_t off_prep = take(cur, sizeof(PrepInstance));
   const size_t off_fin = take(cur, sizeof(FinalInstance));
   const size_t off_seg = take(cur, segment_table_bytes(1));
+  const size_t off_tab = take(cur, (size_t)n3 * 2);
+  const size_t off_off = take(cur, (size_t)(np + 1) * 4);
   const size_t small_end = up(cur, 256);
   if (small_end > kNoallocScratchBytes) return EIK_EBUDGET;  // grid too large for the scratch
   if (small_end - small_begin > sizeof(g_host_small)) return EIK_EBUDGET;
@@ -222,6 +224,20 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   fi->ncy = ncy;
   fi->ncz = ncz;
   fi->n = n;
+  {
+    unsigned short* tab = reinterpret_cast<unsigned short*>(hp(off_tab));
+    int* off = reinterpret_cast<int*>(hp(off_off));
+    int t = 0;
+    for (int C = 0; C < np; ++C) {
+      off[C] = t;
+      for (int c = 0; c < n; ++c)
+        for (int b = 0; b < n; ++b) {
+          const int a = C - b - c;
+          if (a >= 0 && a < n) tab[t++] = (unsigned short)(a + n * (b + n * c));
+        }
+    }
+    off[np] = t;
+  }
 
   Segments segs;
   {
@@ -266,6 +282,8 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.tmaps = reinterpret_cast<const CUtensorMap*>(A + off_tmap);
   p.cells = cells;
   p.ctl = dctl;
+  p.plane_tab = reinterpret_cast<const unsigned short*>(A + off_tab);
+  p.plane_off = reinterpret_cast<const int*>(A + off_off);
   p.spin_cap_ns = 5000000000ull;
   p.max_sweeps = 4096;
   p.pass = 0;

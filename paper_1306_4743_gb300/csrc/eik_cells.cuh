@@ -572,7 +572,34 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       }
     }
     phase ^= 1u;
+    unsigned* fmin = reinterpret_cast<unsigned*>(wshared + 2);  // [6] halo face minima
+    if constexpr (!REPLACE) {
+      if (tid < 6) fmin[tid] = 0xffffffffu;
+    }
     worker_sync<WPC>(worker);
+    // Min mode: the smallest halo value of each face (as ordered float
+    // bits), to start with the sweep direction that runs away from the
+    // lower face on each axis.
+    if constexpr (!REPLACE) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const int axis = f >> 1, side = (f & 1) ? N + 1 : 0;
+        unsigned m = 0xffffffffu;
+        for (int q = tid; q < N * N; q += NT) {
+          const int a = q % N + 1, b = q / N + 1;
+          const int t = axis == 0 ? side + G::SY * a + G::SZ * b
+                      : axis == 1 ? a + G::SY * side + G::SZ * b
+                                  : a + G::SY * b + G::SZ * side;
+          float v;
+          if constexpr (sizeof(T) == 8) v = f32_of_f64_nn(U[t]);
+          else v = U[t];
+          const unsigned vb = __float_as_uint(v);
+          m = vb < m ? vb : m;
+        }
+        m = __reduce_min_sync(0xffffffffu, m);
+        if ((tid & 31) == 0 && m != 0xffffffffu) atomicMin(fmin + f, m);
+      }
+    }
     if (revisit) {
       for (int f = 0; f < 6; ++f) {
         if (!((faces >> f) & 1u)) continue;
@@ -594,10 +621,12 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     }
 
     // ---- 3. sweeps -----------------------------------------------------
-    // Min mode: the first preferred direction (in the standard order), then
-    // each next sweep reverses the axes along which the last one left
-    // active nodes behind.  Replace mode: every preferred direction, then
-    // the standard loop.  A sweep
+    // Min mode: first the direction that leaves the lower halo face behind
+    // on each axis (the cell's inflow side; upward on an axis without halo
+    // values) if it is a preferred direction, else the first preferred one
+    // (in the standard order); then each next sweep reverses the axes along
+    // which the last one left active nodes behind.  Replace mode: every
+    // preferred direction, then the standard loop.  A sweep
     // covers only the planes from the first one holding an active node.
     int nsw = 0;
     bool converged = false;
@@ -629,12 +658,34 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
                                                    worker, kappa, n_updates);
       ++nsw;
     };
-    for (int r = 0; r < 8 && !converged; ++r) {
-      const int d = kStdOrder[r];
-      if (!((pref >> d) & 1u)) continue;  // bits 0-7: preferred directions
-      run(d);
-      if (!lm) converged = true;
-      if (!REPLACE) break;  // min mode: the first one, then the adaptive order
+    if constexpr (!REPLACE) {
+      // min mode: the direction leaving the lower halo face behind on each
+      // axis with halo values (upward where neither face has one), when it
+      // is a preferred direction or none is given; else the first preferred
+      worker_sync<WPC>(worker);  // fmin complete
+      int d0 = 0;
+#pragma unroll
+      for (int axis = 0; axis < 3; ++axis)
+        if (fmin[2 * axis + 1] < fmin[2 * axis]) d0 |= 1 << axis;
+      if (!converged && (((pref >> d0) & 1u) || !(pref & kDirMask))) {
+        run(d0);
+        if (!lm) converged = true;
+      } else {
+        for (int r = 0; r < 8 && !converged; ++r) {
+          const int d = kStdOrder[r];
+          if (!((pref >> d) & 1u)) continue;  // bits 0-7: preferred directions
+          run(d);
+          if (!lm) converged = true;
+          break;
+        }
+      }
+    } else {
+      for (int r = 0; r < 8 && !converged; ++r) {
+        const int d = kStdOrder[r];
+        if (!((pref >> d) & 1u)) continue;  // bits 0-7: preferred directions
+        run(d);
+        if (!lm) converged = true;
+      }
     }
     for (int r = 0; !converged; r = (r + 1) & 7) {
       if (nsw >= p.max_sweeps) break;

@@ -601,15 +601,21 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       }
     }
     if (revisit) {
+      // a flagged face's nodes restart; in min mode only those whose halo
+      // neighbour is below them, as no other can take a lower value from it
       for (int f = 0; f < 6; ++f) {
         if (!((faces >> f) & 1u)) continue;
         const int axis = f >> 1, side = (f & 1) ? N - 1 : 0;
+        const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
         for (int q = tid; q < N * N; q += NT) {
           const int a = q % N, b = q / N;
-          const int e = axis == 0 ? side + N * (a + N * b)
-                      : axis == 1 ? a + N * (side + N * b)
-                                  : a + N * (b + N * side);
-          chg[e] = kActive;
+          int i, j, k;
+          if (axis == 0) { i = side; j = a; k = b; }
+          else if (axis == 1) { i = a; j = side; k = b; }
+          else { i = a; j = b; k = side; }
+          const int e = i + N * (j + N * k);
+          const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+          if (REPLACE || vlt(U[side ? t + step : t - step], U[t])) chg[e] = kActive;
         }
       }
       worker_sync<WPC>(worker);

@@ -89,7 +89,7 @@ typedef struct {
                                (default) */
   double bulk_kappa_rel;    /* EIK_FP32_POLISH only: change threshold of the
                                FP32 bulk sweeps, in units of (cell edge x mean
-                               slowness) (default 1e-3).  Stopping the bulk
+                               slowness) (default 1e-2).  Stopping the bulk
                                early leaves values high, never low, and the
                                FP64 polish starts above the fixed point, so
                                this trades bulk sweeps for polish sweeps and

@@ -758,7 +758,7 @@ int eik_opts_default(eik_opts* o) {
   o->spin_cap_us = 5000000ull;
   o->bucket_width = 0.25;
   o->max_sweeps_per_visit = 4096;
-  o->bulk_kappa_rel = 1.0e-3;
+  o->bulk_kappa_rel = 1.0e-2;
   o->queue_order = 1;
   o->use_graphs = 1;
   return EIK_OK;

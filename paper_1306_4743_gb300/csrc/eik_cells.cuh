@@ -579,8 +579,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     worker_sync<WPC>(worker);
     // Min mode: the smallest halo value of each face (as ordered float
     // bits), to start with the sweep direction that runs away from the
-    // lower face on each axis: a cheap use of the border values to narrow
-    // the preferred directions, which Sec. 4 notes as possible.
+    // lower face on each axis.
     if constexpr (!REPLACE) {
 #pragma unroll
       for (int f = 0; f < 6; ++f) {

@@ -266,7 +266,9 @@ class Solver:
     # -- one grid ---------------------------------------------------------
     def solve(self, F, mask, q, h, tol=0.0, out=None, stream=None, check=True):
         """Solve one grid.  numpy inputs -> eik_solve (host buffers, numpy
-        result); torch CUDA tensors -> eik_solve_device (result tensor).
+        result; page-locked buffers, e.g. the .numpy() views of pinned torch
+        tensors, are read and written in place by the device instead of
+        copied); torch CUDA tensors -> eik_solve_device (result tensor).
         Returns (u, stats_dict)."""
         st = Stats()
         if _is_torch_cuda(F):
@@ -361,7 +363,9 @@ class Solver:
     def submit(self, F, mask, q, h, tol=0.0, out=None):
         """Queue one solve; returns (ticket, out array filled on completion).
         The binding keeps the input and output arrays alive until the ticket
-        is done or cancelled (the library uses them asynchronously)."""
+        is done or cancelled (the library uses them asynchronously).  A
+        page-locked `out` is written in place by the device; cancelling such
+        a request while it runs waits for its batch."""
         F_h, m_h, q_h = _host_arrays(F, mask, q)
         u = out if out is not None else np.empty(F_h.shape, dtype=np.float64)
         if not (u.flags.c_contiguous and u.dtype == np.float64 and u.shape == F_h.shape):

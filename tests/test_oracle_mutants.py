@@ -74,7 +74,8 @@ def _pin_tiny_brute_force():
         mask.reshape(-1)[rng.integers(0, F.size)] = 1
         U = oracle.fmm(F, mask, q, 0.1)
         V, _ = oracle.value_iteration(F, mask, q, 0.1)
-        assert np.max(np.abs(U - V)) <= 1e-14 * U.max()
+        with np.errstate(invalid="ignore"):  # a mutant may leave inf - inf
+            assert np.max(np.abs(U - V)) <= 1e-14 * U.max()
 
 
 def _pin_exact_1d():
@@ -90,7 +91,8 @@ def _pin_table5_head():
     p = W.paper_example(2, 24)
     U, sweeps, mc, nc = oracle.fsm(p.F, p.mask, p.q, p.h, dir_order=(0, 1, 3, 2, 4, 5, 7, 6))
     V = oracle.fmm(p.F, p.mask, p.q, p.h)
-    assert np.max(np.abs(U - V)) <= 1e-13 * V.max()
+    with np.errstate(invalid="ignore"):  # a mutant may leave inf - inf
+        assert np.max(np.abs(U - V)) <= 1e-13 * V.max()
 
 
 def _pin_exit_dirichlet():

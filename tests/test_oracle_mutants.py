@@ -44,6 +44,18 @@ MUTANTS = [
      "if (k + 1 < nz && V[c + nx * ny] < m) m = V[c + nx * ny];", ""),
     ("exit nodes recomputed in FMM",
      "      if (accepted[y] || mask[y]) continue;", "      if (accepted[y]) continue;"),
+    ("residual takes a signed difference",
+     "double e = fabs(U[x] - v);", "double e = U[x] - v;"),
+    ("residual keeps the smallest difference",
+     "if (e > r) r = e;", "if (e < r) r = e;"),
+    ("residual includes exit nodes",
+     "        if (mask[x]) continue;\n        double ax, ay, az;\n        axis_minima(U, i, j, k,",
+     "        double ax, ay, az;\n        axis_minima(U, i, j, k,"),
+    ("residual does not count non-finite values",
+     "if (!isfinite(U[x])) { ++bad; continue; }", "if (!isfinite(U[x])) continue;"),
+    ("residual uses s = F / h",
+     "double v = orc_local_solve(ax, ay, az, h / (double)F[x]);\n        double e",
+     "double v = orc_local_solve(ax, ay, az, (double)F[x] / h);\n        double e"),
 ]
 
 
@@ -106,8 +118,48 @@ def _pin_exit_dirichlet():
     assert U[0, 0, 1] == 3.0
 
 
+def _pin_residual():
+    # closed-form residuals of perturbed exact solutions (see
+    # test_oracle_residual.py): a raised interior node and a lowered end
+    # node of the exact 1D line give delta, an inconsistent exit gives 0,
+    # non-finite values are counted
+    N, h = 30, 1.0 / 29
+    f = np.linspace(0.6, 1.4, N).astype(np.float32)
+    F = f.reshape(1, 1, N)
+    mask = np.zeros(F.shape, np.uint8)
+    mask[0, 0, 3] = 1
+    s = h / f.astype(np.float64)
+    U = np.empty(N)
+    U[3] = 0.0
+    for i in range(4, N):
+        U[i] = U[i - 1] + s[i]
+    for i in range(2, -1, -1):
+        U[i] = U[i + 1] + s[i]
+    delta = 1e-3
+    for node, sign in ((15, 1.0), (N - 1, -1.0)):
+        V = U.copy()
+        V[node] += sign * delta
+        r, bad = oracle.residual(V.reshape(F.shape), F, mask, h)
+        assert bad == 0 and abs(r - delta) <= 1e-14
+    m2 = mask.copy()
+    m2[0, 0, 20] = 1
+    q2 = np.zeros(F.shape)
+    q2[0, 0, 20] = 5.0
+    W2 = U.copy()
+    W2[20] = 5.0
+    for i in range(21, N):
+        W2[i] = W2[i - 1] + s[i]
+    r, bad = oracle.residual(W2.reshape(F.shape), F, m2, h)
+    assert bad == 0 and r == 0.0
+    V = U.copy()
+    V[0] = np.inf
+    V[N - 1] = np.nan
+    r, bad = oracle.residual(V.reshape(F.shape), F, mask, h)
+    assert bad == 2
+
+
 PINS = [_pin_closed_forms, _pin_equation, _pin_tiny_brute_force, _pin_exact_1d,
-        _pin_table5_head, _pin_exit_dirichlet]
+        _pin_table5_head, _pin_exit_dirichlet, _pin_residual]
 
 
 def test_unmutated_oracle_passes_quick_pins():

@@ -1,18 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: converged grid nodes/s of the GB300 parallel Heap-Cell solver.
 
-Default workload (one GPU): the 257^3 unit cube with F = 1 + 0.5 sin(4 pi x)
-sin(4 pi y) sin(4 pi z), exit node at the centre, FP32 bulk sweeps + FP64
-polish.  One step = one whole solve (init, bulk cell kernel, polish cell
-kernel, residual check, copy-out) with F / mask / q already in HBM.
+Default workload (one GPU): the 513^3 barrier-block field (16 boxes a side,
+each slow with F = 0.01 with probability 0.3, else F = 1; 8 exit nodes in
+fast boxes), FP32 bulk sweeps + FP64 polish, kappa 1e-12.  One step = one
+whole solve (init, bulk cell kernel, polish hand-over, polish cell kernel,
+residual check, copy-out) with F / mask / q already in HBM.  The result is
+compared node by node with the CPU oracle's FP64 Fast Marching solution,
+which a spawned worker computes (about two minutes on one core) while the
+GPU legs run; that solve is also the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload barrier513|osc257|point65] [--precision ...]
 
 Prints one JSON line (rank 0).  N > 1 runs under torchrun: the single-grid
 solve does not shard, so every rank solves its own replica (weak scaling)
-and `value` sums the nodes of all ranks over the slowest rank's time.
-`--impl reference` times the CPU oracle (serial FP64 Fast Marching) on a
-bounded sample of the same workload on one host core.
+and `value` sums the nodes of all ranks over the slowest rank's time; the
+256-instance batch is split across ranks by instance.  `--impl reference`
+times the CPU oracle (serial FP64 Fast Marching) on a bounded sample of the
+same workload on one host core.
 """
 import argparse
 import hashlib
@@ -30,38 +36,64 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged grid nodes/s at ≤1e-9 err vs FP64 FMM; serve p50/p99 latency"
 L2_FLUSH_BYTES = 256 << 20
+BOUND = {"fp64": 1e-10, "fp32_polish": 1e-9}  # max |u - u_FMM| / max u
+
+WORKLOADS = {
+    # name: (oracle recipe, edge, description)
+    "barrier513": ("barrier", 513,
+                   "513^3 barrier-block field: unit cube in 16^3 boxes, each slow (F=0.01) with "
+                   "p=0.3 (seed 3), else F=1; 8 exit nodes in fast boxes (seed 33)"),
+    "osc257": ("osc", 257,
+               "257^3 unit cube, F=1+0.5 sin(4 pi x) sin(4 pi y) sin(4 pi z), exit node at the "
+               "centre"),
+    "point65": ("point", 65, "65^3 unit cube, F=1, exit node at the centre"),
+}
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--edge", type=int, default=257)
+    ap.add_argument("--workload", default="barrier513", choices=sorted(WORKLOADS))
+    ap.add_argument("--edge", type=int, default=0,
+                    help="grid edge of the headline recipe (0 = the workload's own)")
     ap.add_argument("--cell-n", type=int, default=0)
-    ap.add_argument("--precision", default="fp64", choices=["fp32_polish", "fp64"],
-                    help="path of the headline single-instance solve (the other one is "
-                         "timed among the extras)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32_polish", choices=["fp32_polish", "fp64"],
+                    help="path of the headline solve (the other one is timed among the extras)")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="no oracle solves (no CPU baseline, no errors against the FMM)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FP64-path and batch comparison lines")
+                    help="only the headline line: no batch, serving or comparison legs")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--serve-unique", type=int, default=24)
+    ap.add_argument("--oracle-jobs", type=int, default=8,
+                    help="oracle worker processes (spawned before any CUDA call)")
     ap.add_argument("--tol", type=float, default=1e-12,
                     help="kappa of the FP64 sweeps (early-termination threshold)")
     return ap.parse_args()
 
 
-def workload(edge):
-    from paper_1306_4743_gb300 import workloads as W
-    return W.oscillatory(edge, 4.0 * math.pi, 0.5)
+def headline(args):
+    """(oracle recipe, edge) of the headline workload."""
+    rec, edge, _ = WORKLOADS[args.workload]
+    return rec, (args.edge or edge)
 
 
-def workload_desc(edge, precision):
-    return ("%d^3 unit cube, F=1+0.5 sin(4 pi x) sin(4 pi y) sin(4 pi z), exit node at "
-            "the centre, %s" % (edge, "FP32 sweeps + FP64 polish" if precision == "fp32_polish"
-                                else "FP64 sweeps"))
+def make_problem(rec, edge):
+    from oracle import fmm_cache  # the recipes only; no oracle arithmetic here
+    return fmm_cache.problem(rec, edge)
+
+
+def workload_desc(args):
+    rec, edge = headline(args)
+    d = WORKLOADS[args.workload][2]
+    if edge != WORKLOADS[args.workload][1]:
+        d = "%d^3 grid of the recipe of: %s" % (edge, d)
+    return "%s; %s" % (d, "FP32 sweeps + FP64 polish" if args.precision == "fp32_polish"
+                       else "FP64 sweeps")
 
 
 def peaks():
@@ -73,10 +105,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic bytes of one cell visit: read the cell and its face halo of u,
-# read the cell's slowness, write the cell's u, ~32 B of queue / state words.
-def bytes_per_visit(n, es):
-    return es * (n ** 3 + 6 * n * n) + es * n ** 3 + es * n ** 3 + 32
+# Algorithmic bytes of one cell visit: read the cell and its face halo of u
+# (es_u bytes per value), read the cell's speed input (4 B per node: the
+# slowness h / F carries no more information than F), write the cell's u,
+# and ~32 B of queue / state words.
+def bytes_per_visit(n, es_u):
+    return es_u * (n ** 3 + 6 * n * n) + 4 * n ** 3 + es_u * n ** 3 + 32
 
 
 # The sources that define the cell kernel: a traffic figure recorded in
@@ -95,9 +129,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag, n):
+def profiled_traffic(kernel_tag, n, workload):
     """DRAM bytes per launch recorded by an ncu capture in profiles/, or None
-    when no capture exists for the current kernel sources."""
+    when no capture of this workload exists for the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -105,9 +139,10 @@ def profiled_traffic(kernel_tag, n):
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 5 and parts[0] == kernel_tag and parts[1] == str(n) \
-                    and parts[2] == src:
-                return {"bytes_per_launch": float(parts[3]), "workload": parts[4]}
+            if (len(parts) >= 5 and parts[0] == kernel_tag and parts[1] == str(n)
+                    and parts[2] == src and parts[4] == workload):
+                return {"bytes_per_launch": float(parts[3]), "workload": parts[4],
+                        "how": " ".join(parts[5:])}
     return None
 
 
@@ -163,24 +198,59 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
 
 
+class OracleJobs:
+    """Oracle FMM solves in spawned worker processes (oracle/fmm_cache.py),
+    created before this process touches CUDA.  Every solve is recomputed
+    (force) so that its time is measured in this run."""
+
+    def __init__(self, jobs):
+        from oracle import fmm_cache
+        self.fc = fmm_cache
+        self.pool = fmm_cache.make_pool(jobs)
+        self.futs = {}
+        self.jobs = jobs
+
+    def submit(self, name, arg, n_requests=500):
+        key = (name, arg, n_requests)
+        if key not in self.futs:
+            self.futs[key] = self.pool.submit(self.fc.solve_named, name, arg, n_requests, True)
+        return key
+
+    def get(self, key, timeout=1800):
+        path, dt = self.futs[key].result(timeout=timeout)
+        return self.fc.load(path), dt
+
+    def close(self):
+        self.pool.shutdown(wait=True, cancel_futures=True)
+
+
+def max_rel_err(u, ref):
+    import numpy as np
+    return float(np.max(np.abs(u - ref))) / float(np.max(ref))
+
+
 def run_reference(args):
-    """The oracle (serial FP64 FMM) on one host core, as the reference arm."""
-    world, rank, _ = dist_setup(args)
+    """The oracle (serial FP64 FMM) on one host core, as the reference arm, on
+    a bounded sample of the headline workload: the same recipe on a coarser
+    m^3 grid, m chosen so the whole run takes a few minutes."""
+    world, rank, _ = dist_setup()
     if rank != 0:
         return
     import oracle
+    from oracle import fmm_cache
+    rec, edge = headline(args)
     total_steps = args.steps + args.warmup
     budget = 150.0 / max(total_steps, 1)          # seconds of CPU work per step
     nodes_target = max(33 ** 3, int(0.6e6 * budget))
-    m = max(33, min(args.edge, int(round(nodes_target ** (1 / 3)))))
-    p = workload(m)
+    m = max(33, min(edge, int(round(nodes_target ** (1 / 3)))))
+    p = fmm_cache.problem(rec, m)
     for _ in range(args.warmup):
         oracle.fmm(p.F, p.mask, p.q, p.h)
     times = []
@@ -190,14 +260,14 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times)
     v = p.nodes / t
-    sample = "%d^3 grid of the same speed field (%d nodes), full FMM solve per step" % (m, p.nodes)
+    sample = ("%d^3 grid of the same recipe (%d nodes), full serial FMM solve per step"
+              % (m, p.nodes))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "nodes/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(args.edge, args.precision),
-                   "sample": sample},
+        "config": {"workload": workload_desc(args), "sample": sample},
         "cpu_baseline": {"value": v, "unit": "nodes/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "nodes/s", "h2d_bytes_per_step": 0,
@@ -205,21 +275,53 @@ def run_reference(args):
     }))
 
 
-def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, check=True,
-                precision="fp32_polish", batch_nodes=None):
+def roofline_of(stats, precision, workload_tag):
+    """Roofline line of the dominant cell kernel of a solve (bulk or polish):
+    algorithmic bytes of its visits over its event-timed duration."""
+    n = stats[-1]["cell_n_used"]
+    tb = statistics.mean(s["seconds_bulk"] for s in stats)
+    tp = statistics.mean(s["seconds_polish"] for s in stats)
+    vb = statistics.mean(s["cell_visits"] for s in stats)
+    vp = statistics.mean(s["polish_visits"] for s in stats)
+    es_b = 4 if precision == "fp32_polish" else 8
+    if tb >= tp:
+        kname = "cells_kernel<%s,%d>" % ("float" if es_b == 4 else "double", n)
+        ksec, kvis, kes = tb, vb, es_b
+        ktag = "bulk_f32" if es_b == 4 else "bulk_f64"
+    else:
+        kname, ksec, kvis, kes = "cells_kernel<double,%d> (FP64 polish)" % n, tp, vp, 8
+        ktag = "polish_f64"
+    bpv = bytes_per_visit(n, kes)
+    achieved = kvis * bpv / ksec / 1e9
+    peak, peak_src = peaks()
+    tr = profiled_traffic(ktag, n, workload_tag)
+    return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tr["bytes_per_launch"] if tr else None),
+            "traffic_note": (tr["how"] if tr else "no ncu capture of the current kernel sources"),
+            "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": kvis * bpv,
+            "bytes_per_visit": bpv, "visits_per_launch": kvis,
+            "kernel_ms": ksec * 1e3, "bulk_ms": tb * 1e3, "polish_ms": tp * 1e3}
+
+
+def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, jobs=None,
+                precision="fp32_polish", batch_nodes=None, check_seed=55):
     """Poisson arrivals of solves (cubic edge log-uniform in [33, 385], speed
     fields from the Gaussian-bump family), continuous batching through
     eik_submit / eik_poll under an HBM budget.  Returns latency percentiles
     and throughput.  Requests cycle over `n_unique` generated problems (the
-    first draws of the same edge / seed stream) to bound host memory."""
+    first draws of the same edge / seed stream) to bound host memory.
+
+    Checked against the oracle (when `jobs` is given): every served request
+    of at most 129^3 nodes and a seeded 10% of the larger ones.  Each checked
+    request gets an output buffer of its own (page-locked, allocated before
+    the timed loop), so its result is compared after the loop without any
+    copy inside it."""
     import numpy as np
     import torch
     draws = W.serving_requests(n=n_requests, rate=1.0, seed=5)
     uniq = [W.serving_problem(edge, seed) for (_, edge, seed) in draws[:n_unique]]
-    # request buffers live in page-locked host memory, as a server receiving
-    # into pinned buffers would have them: the device reads F and q in place
-    # and writes each result in place; two output buffers per problem are
-    # recycled (a third request in flight for one problem gets a pageable one)
     keep = []
 
     def pinned(a):
@@ -229,9 +331,21 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
 
     pin_in = [(pinned(p.F), pinned(p.mask), pinned(p.q)) for p in uniq]
     pool = [[pinned(np.empty(p.F.shape, dtype=np.float64)) for _ in range(2)] for p in uniq]
+    rng = np.random.default_rng(check_seed)
+    checked = {}
+    if jobs is not None:
+        for k in range(n_requests):
+            pr = uniq[k % n_unique]
+            if pr.nodes <= 129 ** 3 or rng.random() < 0.1:
+                checked[k] = pinned(np.empty(pr.F.shape, dtype=np.float64))
+        for k in checked:
+            jobs.submit("serve", k % n_unique, n_requests)
 
-    def submit(s, k):
+    def submit(s, k, own=None):
         F, m, q = pin_in[k]
+        if own is not None:
+            t, u = s.submit(F, m, q, uniq[k].h, tol=tol, out=own)
+            return t, u, False
         buf = pool[k].pop() if pool[k] else None
         t, u = s.submit(F, m, q, uniq[k].h, tol=tol, out=buf)
         return t, u, buf is not None
@@ -262,13 +376,13 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
             closed_nodes = sum(p.nodes for p in uniq) / closed_span
         rate = 0.7 * closed
         arrivals = [a for (a, _, _) in W.serving_requests(n=n_requests, rate=rate, seed=5)]
-        lat, nodes, out, kept = [], 0, {}, {}
+        lat, nodes, out = [], 0, {}
         nxt = 0
         t0 = time.perf_counter()
         while len(lat) < n_requests:
             now = time.perf_counter() - t0
             while nxt < n_requests and arrivals[nxt] <= now:
-                t, u, pooled = submit(s, nxt % n_unique)
+                t, u, pooled = submit(s, nxt % n_unique, checked.get(nxt))
                 out[t] = (nxt, arrivals[nxt], u, pooled)
                 nxt += 1
             for t in list(out):
@@ -279,36 +393,59 @@ def run_serving(eik, W, device, n_requests, n_unique, tol=0.0, budget_gb=120.0, 
                         raise RuntimeError("serving request %d failed: %d" % (k, rc))
                     lat.append(time.perf_counter() - t0 - arr)
                     nodes += uniq[k % n_unique].nodes
-                    if check and k < n_unique and uniq[k].nodes <= 129 ** 3 and k % 3 == 0:
-                        kept[k] = u.copy()  # checked against the oracle after the timed loop
                     if pooled:
                         pool[k % n_unique].append(u)
             if not out and nxt < n_requests:
                 time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.002)))
         span = time.perf_counter() - t0
-    if kept:
-        import oracle
-        for k, u in kept.items():
-            pr = uniq[k]
-            ref = oracle.fmm(pr.F, pr.mask, pr.q, pr.h)
-            e = float(np.max(np.abs(u - ref)) / np.max(ref))
-            if e > 1e-9:
+    worst = None
+    if checked:
+        worst = 0.0
+        for k, u in checked.items():
+            ref, _ = jobs.get(("serve", k % n_unique, n_requests))
+            e = max_rel_err(u, ref)
+            if e > BOUND[precision]:
                 raise RuntimeError("serving request %d error %.2e" % (k, e))
+            worst = max(worst, e)
     lat_ms = np.sort(np.array(lat)) * 1e3
+    big = sum(1 for k in checked if uniq[k % n_unique].nodes > 129 ** 3)
     return {"requests": n_requests, "unique_problems": n_unique,
             "rate_per_s": rate, "closed_loop_per_s": closed,
             "closed_loop_nodes_per_s": closed_nodes,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "nodes_per_s": nodes / span, "budget_gb": budget_gb, "precision": precision,
-            "batch_nodes": batch_nodes, "checked_vs_oracle": len(kept),
+            "batch_nodes": batch_nodes,
+            "checked_vs_oracle": len(checked), "checked_larger_than_129^3": big,
+            "max_rel_err_vs_oracle": worst,
             "request_buffers": "page-locked host memory (inputs read and results written in place)",
             "edges": "cubic, round(exp(U[ln 33, ln 385])), seed 5; F: 8 Gaussian bumps, seed 5000+k"}
 
 
+def time_solves(solver, args_, tol, flush, reps, out=None):
+    ts, sts = [], []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        u, st = solver.solve(*args_, tol=tol, out=out)
+        ts.append(st["seconds"])
+        sts.append(st)
+    return u, ts, sts
+
+
 def run_ours(args):
+    world, rank, local = dist_setup()
+    jobs = None
+    rec, edge = headline(args)
+    if rank == 0 and not args.no_cpu_baseline:
+        # spawned before this process makes any CUDA call
+        jobs = OracleJobs(args.oracle_jobs)
+        head_key = jobs.submit(rec, edge)
+        if not args.no_extras:
+            jobs.submit("osc", 257)
+            jobs.submit("point", 65)
+            for k in range(256):
+                jobs.submit("batch", k)
     import numpy as np
     import torch
-    world, rank, local = dist_setup(args)
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -316,8 +453,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1306_4743_gb300 import eik
+    from paper_1306_4743_gb300 import workloads as W
 
-    p = workload(args.edge)
+    p = make_problem(rec, edge)
     F_d = torch.from_numpy(p.F).to(dev)
     m_d = torch.from_numpy(p.mask).to(dev)
     q_d = torch.from_numpy(p.q).to(dev)
@@ -367,6 +505,7 @@ def run_ours(args):
     t_step = statistics.mean(ev_ms) * 1e-3
     t_max = max_over_ranks(t_step)
     value = world * p.nodes / t_max
+    u_head = u_d.cpu().numpy() if rank == 0 else None
 
     # end to end through the host-buffer entry point (pinned host memory)
     F_h = torch.from_numpy(p.F).pin_memory()
@@ -386,195 +525,35 @@ def run_ours(args):
     e2e_value = world * p.nodes / max_over_ranks(statistics.mean(e2e_t))
     h2d = p.F.nbytes + p.mask.nbytes + p.q.nbytes
     d2h = p.nodes * 8
+    del F_h, m_h, q_h, u_h, Fn, mn, qn, un
 
-    # roofline of the dominant cell kernel
+    roofline = roofline_of(stats, args.precision, args.workload)
     last = stats[-1]
     n = last["cell_n_used"]
-    tb = statistics.mean(s["seconds_bulk"] for s in stats)
-    tp = statistics.mean(s["seconds_polish"] for s in stats)
-    vb = statistics.mean(s["cell_visits"] for s in stats)
-    vp = statistics.mean(s["polish_visits"] for s in stats)
-    es_b = 4 if args.precision == "fp32_polish" else 8
-    if tb >= tp:
-        kname, ksec, kvis, kes = ("cells_kernel<%s,%d>" % ("float" if es_b == 4 else "double", n),
-                                  tb, vb, es_b)
-        ktag = "bulk_f32" if es_b == 4 else "bulk_f64"
-    else:
-        kname, ksec, kvis, kes = "cells_kernel<double,%d> (FP64 polish)" % n, tp, vp, 8
-        ktag = "polish_f64"
-    bpv = bytes_per_visit(n, kes)
-    achieved = kvis * bpv / ksec / 1e9
-    peak, peak_src = peaks()
-    tr = profiled_traffic(ktag, n)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tr["bytes_per_launch"] if tr else None),
-                "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": kvis * bpv,
-                "bytes_per_visit": bpv, "visits_per_launch": kvis,
-                "kernel_ms": ksec * 1e3}
 
-    # parity of the timed result against the oracle, and the CPU baseline
+    extras, u_other = {}, None
+    if not args.no_extras:
+        extras, u_other = run_extras(args, eik, W, torch, np, dev, local, rank, world, flush,
+                                     jobs, barrier, max_over_ranks, p)
+
+    # errors against the oracle and the CPU baseline (the oracle worker ran
+    # while the GPU legs above did)
     cpu = None
     err_rel = None
-    ref = None
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        t0 = time.perf_counter()
-        ref = oracle.fmm(p.F, p.mask, p.q, p.h)
-        tc = time.perf_counter() - t0
-        u = u_d.cpu().numpy()
-        err_rel = float(np.max(np.abs(u - ref)) / np.max(ref))
-        cpu = {"value": p.nodes / tc, "unit": "nodes/s", "cores": 1, "kind": "oracle",
-               "sample": "full %d^3 solve (serial FP64 FMM, binary heap), %.1f s; host has "
-                         "%d cores" % (args.edge, tc, os.cpu_count() or 0)}
-
-    extras = {}
-    if not args.no_extras:
-        # the batch of 256 uneven instances; under torchrun each rank solves
-        # its share (greedy by size, no collective decides the split)
-        from paper_1306_4743_gb300 import dispatch
-        from paper_1306_4743_gb300 import workloads as W
-        probs = W.batch_instances(256)
-        mine = dispatch.shard([b.nodes for b in probs], rank, world)
-        bt = [(torch.from_numpy(probs[k].F).to(dev), torch.from_numpy(probs[k].mask).to(dev),
-               torch.from_numpy(probs[k].q).to(dev), probs[k].h) for k in mine]
-        bnodes = sum(b.nodes for b in probs)
-        # the FP64-path batch first, for comparison
-        with eik.Solver(precision="fp64", device=local) as sb:
-            outs, st = sb.solve_batch_device(bt, tol=args.tol)
-            ts = []
-            for _ in range(3):
-                flush.fill_(1.0)
-                barrier()
-                outs, st = sb.solve_batch_device(bt, tol=args.tol, outs=outs)
-                ts.append(st["seconds"])
-        tb64 = max_over_ranks(statistics.mean(ts))
-        extras["batch256_fp64"] = {"nodes": bnodes, "nodes_per_s": bnodes / tb64,
-                                   "ms": tb64 * 1e3, "ranks": world}
-        # the FP32 + FP64-polish batch (one persistent launch per rank)
-        with eik.Solver(precision="fp32_polish", device=local) as sb:
-            outs, st = sb.solve_batch_device(bt, tol=args.tol)
-            ts = []
-            for _ in range(3):
-                flush.fill_(1.0)
-                barrier()
-                outs, st = sb.solve_batch_device(bt, tol=args.tol, outs=outs)
-                ts.append(st["seconds"])
-        tbatch = max_over_ranks(statistics.mean(ts))
-        batch_err = None
-        if rank == 0 and cpu is not None:
-            import oracle
-            errs = []
-            for k in (0, 100, 255):
-                if k not in mine:
-                    continue
-                r = oracle.fmm(probs[k].F, probs[k].mask, probs[k].q, probs[k].h)
-                o = outs[mine.index(k)]
-                errs.append(float(np.max(np.abs(o.cpu().numpy() - r)) / np.max(r)))
-            batch_err = max(errs) if errs else None
-        extras["batch256"] = {
-            "precision": "fp32_polish",
-            "nodes": bnodes, "nodes_per_s": bnodes / tbatch,
-            "ms": tbatch * 1e3, "cell_n": st["cell_n_used"], "ranks": world,
-            "instances_rank0": len(mine),
-            "max_rel_err_vs_oracle_sampled": batch_err}
-        del bt, outs
-    if rank == 0 and not args.no_extras:
-        # the other precision mode, single instance, on the same grid (rank 0)
-        other = "fp32_polish" if args.precision == "fp64" else "fp64"
-        u64 = torch.empty_like(u_d)
-        with eik.Solver(precision=other, cell_n=args.cell_n, device=local) as s64:
-            s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
-            ts, tbo, tpo = [], [], []
-            for _ in range(5):
-                flush.fill_(1.0)
-                _, st = s64.solve(F_d, m_d, q_d, p.h, tol=args.tol, out=u64)
-                ts.append(st["seconds"])
-                tbo.append(st["seconds_bulk"])
-                tpo.append(st["seconds_polish"])
-        extras[other + "_single_instance"] = {
-            "nodes_per_s": p.nodes / statistics.mean(ts), "ms": statistics.mean(ts) * 1e3,
-            "bulk_ms": statistics.mean(tbo) * 1e3, "polish_ms": statistics.mean(tpo) * 1e3,
-            "max_rel_err_vs_oracle": (float(np.max(np.abs(u64.cpu().numpy() - ref)) / np.max(ref))
-                                      if cpu is not None else None)}
-        # early termination (Sec. 6.4): error against the oracle and time per kappa
-        if cpu is not None:
-            sweep = []
-            for kap in (0.0, 1e-14, 1e-12, 1e-10, 1e-8, 1e-6):
-                row = {"tol": kap}
-                for prec in ("fp32_polish", "fp64"):
-                    uk = torch.empty_like(u_d)
-                    with eik.Solver(precision=prec, device=local) as sk:
-                        sk.solve(F_d, m_d, q_d, p.h, tol=kap, out=uk)
-                        ts = []
-                        for _ in range(2):
-                            flush.fill_(1.0)
-                            _, st = sk.solve(F_d, m_d, q_d, p.h, tol=kap, out=uk)
-                            ts.append(st["seconds"])
-                    row[prec] = {"ms": statistics.mean(ts) * 1e3,
-                                 "max_rel_err_vs_oracle":
-                                     float(np.max(np.abs(uk.cpu().numpy() - ref)) / np.max(ref))}
-                sweep.append(row)
-            extras["kappa_sweep"] = sweep
-        # the paper's synchronous comparator: whole-grid plane-parallel sweeping
-        ud = torch.empty_like(u_d)
-        eik.dfsm_solve(F_d, m_d, q_d, p.h, tol=args.tol, out=ud)
-        _, std = eik.dfsm_solve(F_d, m_d, q_d, p.h, tol=args.tol, out=ud)
-        extras["dfsm_single_instance"] = {
-            "nodes_per_s": p.nodes / std["seconds"], "ms": std["seconds"] * 1e3,
-            "sweeps": std["sweeps"],
-            "max_rel_err_vs_oracle": (float(np.max(np.abs(ud.cpu().numpy() - ref)) / np.max(ref))
-                                      if cpu is not None else None)}
-        # the other named workloads: 65^3 point source (FP64, 8^3 cells) and
-        # the 513^3 barrier field (FP32 + FP64 polish; checked by the oracle's
-        # residual at every node, a full FMM of 135 M nodes being too slow here)
-        p1 = W.point_source_const(65)
-        d1 = [torch.from_numpy(x).to(dev) for x in (p1.F, p1.mask, p1.q)]
-        u1 = torch.empty(p1.F.shape, dtype=torch.float64, device=dev)
-        with eik.Solver(precision="fp64", cell_n=8, device=local) as s1:
-            s1.solve(d1[0], d1[1], d1[2], p1.h, tol=args.tol, out=u1)
-            ts = []
-            for _ in range(5):
-                flush.fill_(1.0)
-                _, st = s1.solve(d1[0], d1[1], d1[2], p1.h, tol=args.tol, out=u1)
-                ts.append(st["seconds"])
-        r1 = None
-        if cpu is not None:
-            import oracle
-            f1 = oracle.fmm(p1.F, p1.mask, p1.q, p1.h)
-            r1 = float(np.max(np.abs(u1.cpu().numpy() - f1)) / np.max(f1))
-        extras["point_source_65_fp64"] = {
-            "nodes": p1.nodes, "nodes_per_s": p1.nodes / statistics.mean(ts),
-            "ms": statistics.mean(ts) * 1e3, "cell_n": 8, "max_rel_err_vs_oracle": r1}
-        del d1, u1
-        p3 = W.barrier_blocks(513)
-        d3 = [torch.from_numpy(x).to(dev) for x in (p3.F, p3.mask, p3.q)]
-        u3 = torch.empty(p3.F.shape, dtype=torch.float64, device=dev)
-        with eik.Solver(precision="fp32_polish", device=local) as s3:
-            s3.solve(d3[0], d3[1], d3[2], p3.h, tol=args.tol, out=u3)
-            ts = []
-            for _ in range(3):
-                flush.fill_(1.0)
-                _, st3 = s3.solve(d3[0], d3[1], d3[2], p3.h, tol=args.tol, out=u3)
-                ts.append(st3["seconds"])
-        res3 = None
-        if cpu is not None:
-            import oracle
-            rr, bad = oracle.residual(u3.cpu().numpy(), p3.F, p3.mask, p3.h)
-            res3 = {"max_abs_residual": rr, "nonfinite": bad,
-                    "rel_to_max_u": rr / float(st3["u_max"])}
-        extras["barrier_513_fp32_polish"] = {
-            "nodes": p3.nodes, "nodes_per_s": p3.nodes / statistics.mean(ts),
-            "ms": statistics.mean(ts) * 1e3, "cell_n": st3["cell_n_used"],
-            "fallback_used": st3["fallback_used"], "oracle_residual": res3}
-        del d3, u3
-        extras["serving"] = run_serving(eik, W, local, args.serve_requests,
-                                        args.serve_unique, tol=args.tol,
-                                        check=cpu is not None)
-        extras["serving_fp64"] = run_serving(eik, W, local, args.serve_requests,
-                                             args.serve_unique, tol=args.tol, check=False,
-                                             precision="fp64")
+    if jobs is not None:
+        ref, dt = jobs.get(head_key)
+        err_rel = max_rel_err(u_head, ref)
+        if u_other is not None:
+            other = "fp32_polish" if args.precision == "fp64" else "fp64"
+            extras["headline_" + other]["max_rel_err_vs_oracle"] = max_rel_err(u_other, ref)
+        del ref
+        if err_rel > BOUND[args.precision]:
+            print("warning: max error %.3e above %.0e" % (err_rel, BOUND[args.precision]),
+                  file=sys.stderr)
+        cpu = {"value": p.nodes / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+               "sample": "full %d^3 solve of the same workload (serial FP64 FMM, binary heap), "
+                         "%.1f s, in a worker process on 1 core while the GPU legs ran; host "
+                         "has %d cores" % (edge, dt, os.cpu_count() or 0)}
 
     out = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
@@ -582,11 +561,12 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "fp32_polish" else "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(args.edge, args.precision), "nodes": p.nodes,
+        "config": {"workload": workload_desc(args), "nodes": p.nodes,
                    "cell_n": n, "precision": args.precision, "tol": args.tol,
+                   "error_bound": "max|u - u_FMM| <= %.0e max(u)" % BOUND[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MB L2 flush between steps (outside the step events); the "
-                         "solve's working set (~0.6 GB) also exceeds the 129 MB L2"},
+                         "solve's working set (~3 GB) also exceeds the 129 MB L2"},
         "e2e": {"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "host_io": "page-locked host buffers: F read in place, q read in place at "
@@ -596,25 +576,172 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "max_rel_err_vs_oracle": err_rel,
         "node_updates_per_s": {
             ("bulk_fp32" if args.precision == "fp32_polish" else "bulk_fp64"):
-                statistics.mean(s["node_updates"] for s in stats) / tb if tb else None,
-            "polish_fp64": (statistics.mean(s["polish_node_updates"] for s in stats) / tp
-                            if tp else None)},
+                statistics.mean(s["node_updates"] for s in stats) / roofline["bulk_ms"] * 1e3,
+            "polish_fp64": (statistics.mean(s["polish_node_updates"] for s in stats)
+                            / roofline["polish_ms"] * 1e3 if roofline["polish_ms"] else None)},
         "fallback_used": int(sum(s["fallback_used"] for s in stats)),
-        "visits": {"bulk": vb, "polish": vp, "cells": int(math.ceil(args.edge / n) ** 3)},
-        "max_rel_err_vs_oracle": err_rel,
-        "residual_max": last["residual_max"],
-        "bulk_ms": tb * 1e3, "polish_ms": tp * 1e3,
+        "visits": {"bulk": statistics.mean(s["cell_visits"] for s in stats),
+                   "polish": statistics.mean(s["polish_visits"] for s in stats),
+                   "cells": int(math.ceil(edge / n) ** 3)},
+        "residual_max": last["residual_max"], "u_max": last["u_max"],
         "wall_s_timed_region": wall,
     }
     out.update(extras)
+    if jobs is not None:
+        jobs.close()
     if rank == 0:
         print(json.dumps(out))
     solver.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_extras(args, eik, W, torch, np, dev, local, rank, world, flush, jobs, barrier,
+               max_over_ranks, p_head):
+    """The other named workloads and paths, each timed with CUDA events on
+    device-resident inputs, and compared with the oracle's FMM solution when
+    the oracle workers run (rank 0).  Returns (extras, headline result in the
+    other precision or None)."""
+    from paper_1306_4743_gb300 import dispatch
+    ex = {}
+    tol = args.tol
+
+    def err(u, key):
+        if jobs is None:
+            return None
+        ref, _ = jobs.get(key)
+        return max_rel_err(u, ref)
+
+    # --- the 256-instance batch, both precisions; under torchrun each rank
+    # solves its share (greedy by size, no collective decides the split)
+    probs = W.batch_instances(256)
+    mine = dispatch.shard([b.nodes for b in probs], rank, world)
+    bt = [(torch.from_numpy(probs[k].F).to(dev), torch.from_numpy(probs[k].mask).to(dev),
+           torch.from_numpy(probs[k].q).to(dev), probs[k].h) for k in mine]
+    bnodes = sum(b.nodes for b in probs)
+    for prec in ("fp64", "fp32_polish"):
+        with eik.Solver(precision=prec, device=local) as sb:
+            outs, st = sb.solve_batch_device(bt, tol=tol)
+            ts, sts = [], []
+            for _ in range(5):
+                flush.fill_(1.0)
+                barrier()
+                outs, st = sb.solve_batch_device(bt, tol=tol, outs=outs)
+                ts.append(st["seconds"])
+                sts.append(st)
+        tb = max_over_ranks(statistics.mean(ts))
+        name = "batch256" if prec == "fp32_polish" else "batch256_fp64"
+        row = {"precision": prec, "nodes": bnodes, "nodes_per_s": bnodes / tb,
+               "ms": tb * 1e3, "cell_n": st["cell_n_used"], "ranks": world,
+               "instances_rank0": len(mine), "gpu_launches_per_step": st["kernel_launches"],
+               "roofline": roofline_of(sts, prec, "batch256"),
+               "bulk_visits": st["cell_visits"], "polish_visits": st["polish_visits"],
+               "fallback_used": st["fallback_used"]}
+        if rank == 0 and jobs is not None:
+            row["max_rel_err_vs_oracle"] = max(err(o.cpu().numpy(), ("batch", k, 500))
+                                               for k, o in zip(mine, outs))
+            row["instances_checked_vs_oracle"] = len(mine)
+        ex[name] = row
+        del outs
+    del bt
+    if rank != 0:
+        return ex, None
+    # --- the headline grid in the other precision, single instance
+    F_d = torch.from_numpy(p_head.F).to(dev)
+    m_d = torch.from_numpy(p_head.mask).to(dev)
+    q_d = torch.from_numpy(p_head.q).to(dev)
+    other = "fp32_polish" if args.precision == "fp64" else "fp64"
+    with eik.Solver(precision=other, cell_n=args.cell_n, device=local) as so:
+        so.solve(F_d, m_d, q_d, p_head.h, tol=tol)
+        u, ts, sts = time_solves(so, (F_d, m_d, q_d, p_head.h), tol, flush, 5)
+    ex["headline_" + other] = {
+        "ms": statistics.mean(ts) * 1e3, "nodes_per_s": p_head.nodes / statistics.mean(ts),
+        "bulk_ms": statistics.mean(s["seconds_bulk"] for s in sts) * 1e3,
+        "polish_ms": statistics.mean(s["seconds_polish"] for s in sts) * 1e3,
+        "cell_n": sts[-1]["cell_n_used"], "roofline": roofline_of(sts, other, args.workload)}
+    u_other = u.cpu().numpy()
+    del F_d, m_d, q_d, u
+    # --- 257^3 oscillatory: both modes, autotuned shape, kappa sweep, DFSM
+    p2 = W.oscillatory(257)
+    d2 = [torch.from_numpy(x).to(dev) for x in (p2.F, p2.mask, p2.q)]
+    u2 = torch.empty(p2.F.shape, dtype=torch.float64, device=dev)
+    k2 = ("osc", 257, 500)
+    for prec in ("fp64", "fp32_polish"):
+        with eik.Solver(precision=prec, device=local) as s2:
+            s2.solve(*d2, p2.h, tol=tol, out=u2)
+            _, ts, sts = time_solves(s2, (*d2, p2.h), tol, flush, 5, out=u2)
+            row = {"ms": statistics.mean(ts) * 1e3,
+                   "nodes_per_s": p2.nodes / statistics.mean(ts),
+                   "bulk_ms": statistics.mean(s["seconds_bulk"] for s in sts) * 1e3,
+                   "polish_ms": statistics.mean(s["seconds_polish"] for s in sts) * 1e3,
+                   "cell_n": sts[-1]["cell_n_used"],
+                   "roofline": roofline_of(sts, prec, "osc257"),
+                   "max_rel_err_vs_oracle": err(u2.cpu().numpy(), k2)}
+            # autotuner: cell size and CTAs of the cell kernel for this size
+            bn, bc = s2.autotune(p2.F, p2.mask, p2.q, p2.h, tol=tol)
+            s2.solve(*d2, p2.h, tol=tol, out=u2)
+            _, ts, sts = time_solves(s2, (*d2, p2.h), tol, flush, 5, out=u2)
+            row["autotuned"] = {"cell_n": bn, "ctas": bc, "ms": statistics.mean(ts) * 1e3,
+                                "nodes_per_s": p2.nodes / statistics.mean(ts),
+                                "max_rel_err_vs_oracle": err(u2.cpu().numpy(), k2)}
+        ex["osc257_" + prec] = row
+    sweep = []
+    for kap in (0.0, 1e-14, 1e-12, 1e-10, 1e-8, 1e-6):
+        row = {"tol": kap}
+        for prec in ("fp32_polish", "fp64"):
+            with eik.Solver(precision=prec, device=local) as sk:
+                sk.solve(*d2, p2.h, tol=kap, out=u2)
+                _, ts, _ = time_solves(sk, (*d2, p2.h), kap, flush, 2, out=u2)
+            row[prec] = {"ms": statistics.mean(ts) * 1e3,
+                         "max_rel_err_vs_oracle": err(u2.cpu().numpy(), k2)}
+        sweep.append(row)
+    ex["kappa_sweep_osc257"] = sweep
+    ud = torch.empty_like(u2)
+    eik.dfsm_solve(*d2, p2.h, tol=tol, out=ud)
+    _, std = eik.dfsm_solve(*d2, p2.h, tol=tol, out=ud)
+    ex["dfsm_osc257"] = {"nodes_per_s": p2.nodes / std["seconds"], "ms": std["seconds"] * 1e3,
+                         "sweeps": std["sweeps"], "max_rel_err_vs_oracle": err(ud.cpu().numpy(),
+                                                                               k2)}
+    if jobs is not None:
+        ex["cpu_oracle_osc257"] = {"seconds": jobs.get(k2)[1],
+                                   "nodes_per_s": p2.nodes / jobs.get(k2)[1], "cores": 1}
+    del d2, u2, ud
+    # --- 65^3 point source, FP64, 8^3 cells
+    p1 = W.point_source_const(65)
+    d1 = [torch.from_numpy(x).to(dev) for x in (p1.F, p1.mask, p1.q)]
+    u1 = torch.empty(p1.F.shape, dtype=torch.float64, device=dev)
+    with eik.Solver(precision="fp64", cell_n=8, device=local) as s1:
+        s1.solve(*d1, p1.h, tol=tol, out=u1)
+        _, ts, _ = time_solves(s1, (*d1, p1.h), tol, flush, 5, out=u1)
+    ex["point65_fp64"] = {"nodes": p1.nodes, "nodes_per_s": p1.nodes / statistics.mean(ts),
+                          "ms": statistics.mean(ts) * 1e3, "cell_n": 8,
+                          "max_rel_err_vs_oracle": err(u1.cpu().numpy(), ("point", 65, 500))}
+    del d1, u1
+    # --- cell values of Eq. 3 against Eq. 4 (Sec. 7) on the 64^3 shell maze
+    pm = W.shell_maze(64)
+    dm = [torch.from_numpy(x).to(dev) for x in (pm.F, pm.mask, pm.q)]
+    cells = (64 // 8) ** 3
+    avs = {"workload": "64^3 shell maze (Sec. 6.7), 8^3 cells, FP64, kappa 0"}
+    for key, ck in (("eq3", 0), ("eq4", 1)):
+        with eik.Solver(precision="fp64", cell_n=8, cell_key=ck, device=local) as sm:
+            _, st = sm.solve(*dm, pm.h, tol=0.0)
+        avs[key] = {"visits_per_cell": st["cell_visits"] / cells,
+                    "sweeps_per_cell": st["sweeps"] / cells,
+                    "node_updates_per_node": st["node_updates"] / pm.nodes,
+                    "ms": st["seconds"] * 1e3}
+    ex["cell_value_avs_maze64"] = avs
+    del dm
+    # --- serving, both precisions
+    if not args.no_serving:
+        ex["serving"] = run_serving(eik, W, local, args.serve_requests, args.serve_unique,
+                                    tol=tol, jobs=jobs)
+        ex["serving_fp64"] = run_serving(eik, W, local, args.serve_requests, args.serve_unique,
+                                         tol=tol, jobs=jobs, precision="fp64")
+    return ex, u_other
 
 
 def main():

@@ -272,24 +272,27 @@ int eik_cancel(eik_ctx *ctx, uint64_t ticket);
  * Allocation-free FP64 solve (this entry point has no counterpart in the
  * paper; it exists for the callers below).
  *
- * Some callers cannot allocate device memory while they solve: code that
- * runs while another framework is capturing a CUDA graph (cudaMalloc is not
- * allowed inside a capture), programs whose own allocator owns all device
- * memory, and latency-critical loops where an allocation may stall on a
- * device-wide synchronisation.  eik_solve_device_noalloc needs no context and
- * calls no allocating routine: its working memory is one fixed device array
- * of EIK_NOALLOC_SCRATCH_BYTES inside the library, which every device that
+ * Some callers cannot allocate device memory while they solve: programs
+ * whose own caching allocator has reserved the device memory up front (a
+ * cudaMalloc would fail, or force that allocator to give memory back),
+ * latency-critical loops where an allocation can stall behind a device-wide
+ * synchronisation, and plug-in code whose host framework only lets it use
+ * memory it was handed.  eik_solve_device_noalloc needs no context and calls
+ * no allocating routine: its working memory is one fixed device array of
+ * EIK_NOALLOC_SCRATCH_BYTES inside the library, which every device that
  * loads the library holds until the process exits.
  *
  * Arguments as eik_solve_device (device buffers on the current device,
  * stream = cudaStream_t or NULL); the sweeps run in FP64 with cells of 8^3
- * nodes.  The call returns after the stream has finished the solve; stats
- * (may be NULL) gets the counters and the residual, not the timings.
+ * nodes.  The call enqueues the solve on `stream`, waits for that stream to
+ * finish it and then returns; stats (may be NULL) gets the counters and the
+ * residual, not the timings.
  *
  * Limits and sharing:
  *  - a grid needs about 17 bytes of scratch per node plus padding; larger
- *    grids (above roughly 150^3 nodes for a cube) are rejected with
- *    EIK_EBUDGET before any device work;
+ *    grids (above roughly 150^3 nodes for a cube, and any grid above
+ *    EIK_NOALLOC_SCRATCH_BYTES / 16 nodes) are rejected with EIK_EBUDGET
+ *    before any device work;
  *  - the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture;
@@ -331,7 +334,7 @@ int eik_dfsm_solve_device(const int64_t dims[3], double h, const float *F_dev,
                           double *max_drop_per_sweep, eik_stats *stats);
 
 /*
- * Diagnostic: accuracy of the device local solve of Eq. 2 used
+ * Diagnostic: accuracy of the device local solve of Eq. 2 (Sec. 1.1) used
  * by the FP64 sweeps, against the direct FP64 evaluation of the same root
  * (shifted closed forms with an FP64 square root, the form the residual
  * certificate uses), on `count` inputs drawn on the device from a

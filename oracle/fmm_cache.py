@@ -60,7 +60,9 @@ def digest(p) -> str:
 def problem(name: str, arg: int, n_requests: int = 500):
     """The seeded workload `name` with parameter `arg`:
     ("barrier", m) the barrier-block field on m^3 nodes (16 boxes a side,
-    p = 0.3, F = 0.01, 8 exits); ("batch", k) instance k of the 256-instance
+    p = 0.3, F = 0.01, 8 exits); ("osc", m) the oscillatory speed
+    1 + 0.5 sin(4 pi x) sin(4 pi y) sin(4 pi z) on m^3 nodes; ("point", m) the
+    F = 1 point source on m^3 nodes; ("batch", k) instance k of the 256-instance
     batch; ("serve", k) request k of the serving stream of `n_requests`
     draws (the edges depend on the stream length)."""
     if ROOT not in sys.path:
@@ -68,6 +70,10 @@ def problem(name: str, arg: int, n_requests: int = 500):
     from paper_1306_4743_gb300 import workloads as W
     if name == "barrier":
         return W.barrier_blocks(arg)
+    if name == "osc":
+        return W.oscillatory(arg)
+    if name == "point":
+        return W.point_source_const(arg)
     if name == "batch":
         return W.gaussian_bumps(W.batch_dims(arg + 1)[arg], 4000 + arg)
     if name == "serve":
@@ -76,12 +82,13 @@ def problem(name: str, arg: int, n_requests: int = 500):
     raise ValueError("unknown workload " + name)
 
 
-def cached_fmm(p, mmap: bool = True):
-    """u = orc_fmm(p) from the cache, computing and storing it on a miss.
-    Returns (u, seconds of the FMM solve or None when it came from the cache)."""
+def cached_fmm(p, mmap: bool = True, force: bool = False):
+    """u = orc_fmm(p) from the cache, computing and storing it on a miss (or
+    always, with force, so that the solve is timed).  Returns (u, seconds of
+    the FMM solve or None when it came from the cache)."""
     import oracle
     path = os.path.join(cache_dir(), digest(p) + ".npy")
-    if os.path.exists(path):
+    if os.path.exists(path) and not force:
         return np.load(path, mmap_mode="r" if mmap else None), None
     t0 = time.perf_counter()
     u = oracle.fmm(p.F, p.mask, p.q, p.h)
@@ -93,12 +100,13 @@ def cached_fmm(p, mmap: bool = True):
     return u, dt
 
 
-def solve_named(name: str, arg: int, n_requests: int = 500):
+def solve_named(name: str, arg: int, n_requests: int = 500, force: bool = False):
     """Worker entry: regenerate the problem, take its FMM solution from the
-    cache or compute it.  Returns (cache path, FMM seconds or None)."""
+    cache or compute it (always with force).  Returns (cache path, FMM
+    seconds or None when it came from the cache)."""
     p = problem(name, arg, n_requests)
     path = os.path.join(cache_dir(), digest(p) + ".npy")
-    _, dt = cached_fmm(p)
+    _, dt = cached_fmm(p, force=force)
     return path, dt
 
 

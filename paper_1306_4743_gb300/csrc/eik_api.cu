@@ -61,6 +61,7 @@ struct eik_ctx {
   ServeState* serve = nullptr;
   // autotune results: log2(nodes) bucket -> (cell size, CTAs of the cell kernel)
   std::map<int, std::pair<int, int>> tuned;
+  unsigned long long tune_generation = 0;  // bumped by every eik_autotune
 };
 
 namespace {
@@ -301,11 +302,12 @@ int encode_map(eik_ctx* ctx, CUtensorMap* map, void* base, int es, long long px,
     }                                      \
   } while (0)
 
+// Each edge in [1, 2^24] and at most 2^34 nodes in all; the node count is
+// bounded before it is formed (d0 d1 <= 2^48 fits, d0 d1 d2 might not).
 bool valid_dims(const int64_t* d) {
   for (int a = 0; a < 3; ++a)
     if (d[a] < 1 || d[a] > (1 << 24)) return false;
-  const long long nodes = (long long)d[0] * d[1] * d[2];
-  return nodes <= (1ll << 34);
+  return (long long)d[0] * d[1] <= (1ll << 34) / d[2];
 }
 
 // The device address of a page-locked host buffer (cudaHostAlloc or
@@ -531,10 +533,11 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   Control* dctl = reinterpret_cast<Control*>(A + L.off_ctl);
 
   CK(cudaEventRecord(ex.ev[0], st));
+  int nl = 0;  // kernels enqueued
   double wf = ctx->opts.bucket_width > 0 ? ctx->opts.bucket_width : 0.25;
   CK(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + L.off_prep), segs, L.total_cells,
                       cells, dctl, reinterpret_cast<int*>(A + L.off_nsrc), !polish, n, wf,
-                      ctx->opts.bulk_kappa_rel, st));
+                      ctx->opts.bulk_kappa_rel, st, nl));
 
   CellKernelParams p;
   p.inst = reinterpret_cast<const Instance*>(A + L.off_inst_b);
@@ -558,11 +561,11 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.use_levels = 0;
   CK(cudaEventRecord(ex.ev[1], st));
   int grid_ctas = 0;
-  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas));
+  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas, nl));
   CK(cudaEventRecord(ex.ev[2], st));
   if (polish) {
     CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), segs,
-                          L.total_cells, cells, dctl, st));
+                          L.total_cells, cells, dctl, st, nl));
     p.inst = reinterpret_cast<const Instance*>(A + L.off_inst64);
     p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap64);
     p.pass = 1;
@@ -571,20 +574,20 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     p.use_levels = 1;
     CK(cudaEventRecord(ex.ev[3], st));
     // monotone FP64 sweeps down from the lifted FP32 result
-    CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr));
+    CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr, nl));
     CK(cudaEventRecord(ex.ev[4], st));
     // fallback, gated on the device: if some u ended below the fixed point
     // (lift too small), polish again with replace-mode sweeps
     CK(launch_fallback_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol),
                             reinterpret_cast<const FinalInstance*>(A + L.off_fin), segs,
-                            L.total_cells, cells, dctl, tol, st));
+                            L.total_cells, cells, dctl, tol, st, nl));
     p.pass = 2;
     p.gated = 0;
     p.use_levels = 0;
-    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr));
+    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr, nl));
   }
   CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), segs, dctl,
-                             polish, tol, st));
+                             polish, tol, st, nl));
   CK(cudaEventRecord(ex.ev[5], st));
   Control* hres = reinterpret_cast<Control*>(ex.h_ctl);
   CK(cudaMemcpyAsync(hres, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
@@ -598,6 +601,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   }
   Lr.hres = hres;
   Lr.grid = grid_ctas;
+  Lr.launches = nl;
   return EIK_OK;
 }
 
@@ -644,9 +648,7 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
     stats->nonfinite = hres->nonfinite;
     stats->nodes = (uint64_t)nodes_total;
     stats->cell_n_used = n;
-    // reset, init u, init s, setup, seed, cells [, convert, keys, setup,
-    // seed, cells], residual + copy-out
-    stats->kernel_launches = polish ? 20 : 8;
+    stats->kernel_launches = (uint64_t)Lr.launches;
     stats->grid_ctas = grid_ctas;
     stats->fallback_used = hres->counters[2][kCntPushes] > 0;
     stats->fallback_visits = hres->counters[2][kCntVisits];
@@ -874,7 +876,7 @@ int eik_solve_device(eik_ctx* ctx, const int64_t dims[3], double h, const float*
 int eik_autotune(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
                  const uint8_t* src_mask, const double* q, double tol, int* best_n,
                  int* best_ctas) {
-  if (!ctx || !dims || !F || !src_mask || !q) return EIK_EINVAL;
+  if (!ctx || !dims || !F || !src_mask || !q || !valid_dims(dims)) return EIK_EINVAL;
   const long long nodes = (long long)dims[0] * dims[1] * dims[2];
   double* u = static_cast<double*>(malloc((size_t)nodes * sizeof(double)));
   if (!u) return EIK_ENOMEM;
@@ -905,6 +907,7 @@ int eik_autotune(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
   free(u);
   if (rc != EIK_OK) return rc;
   ctx->tuned[size_bucket(nodes)] = std::make_pair(bn, bc);
+  ++ctx->tune_generation;  // a captured batch graph may hold the old choice
   if (best_n) *best_n = bn;
   if (best_ctas) *best_ctas = bc;
   return EIK_OK;
@@ -939,6 +942,7 @@ int eik_solve_batch_device(eik_ctx* ctx, int count, const int64_t* dims, const d
   memcpy(&tb, &tol, 8);
   key.push_back(tb);
   key.push_back((unsigned long long)(uintptr_t)st);
+  key.push_back(ctx->tune_generation);
   for (int t = 0; t < count; ++t) {
     for (int a = 0; a < 3; ++a) key.push_back((unsigned long long)dims[3 * t + a]);
     unsigned long long hb;

@@ -5,11 +5,11 @@
 namespace eik {
 
 cudaError_t launch_cells_f32(int n, const CellKernelParams& p, int sms, cudaStream_t st,
-                             int* grid_out) {
+                             int* grid_out, int& launches) {
   switch (n) {
-    case 4: return launch_cells_t<float, 4, false>(p, sms, st, grid_out);
-    case 8: return launch_cells_t<float, 8, false>(p, sms, st, grid_out);
-    case 16: return launch_cells_t<float, 16, false>(p, sms, st, grid_out);
+    case 4: return launch_cells_t<float, 4, false>(p, sms, st, grid_out, launches);
+    case 8: return launch_cells_t<float, 8, false>(p, sms, st, grid_out, launches);
+    case 16: return launch_cells_t<float, 16, false>(p, sms, st, grid_out, launches);
     default: return cudaErrorInvalidValue;
   }
 }

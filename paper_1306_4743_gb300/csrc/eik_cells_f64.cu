@@ -5,27 +5,27 @@
 namespace eik {
 
 cudaError_t launch_cells_f32(int n, const CellKernelParams& p, int sms, cudaStream_t st,
-                             int* grid_out);
+                             int* grid_out, int& launches);
 void cells_shape_f32(int n, int* threads, int* smem, int* workers);
 
 cudaError_t launch_cells(bool fp64, bool replace, int n, const CellKernelParams& p, int sms,
-                         cudaStream_t st, int* grid_out) {
+                         cudaStream_t st, int* grid_out, int& launches) {
   if (!fp64) {
     if (replace) return cudaErrorInvalidValue;
-    return launch_cells_f32(n, p, sms, st, grid_out);
+    return launch_cells_f32(n, p, sms, st, grid_out, launches);
   }
   if (replace) {
     switch (n) {
-      case 4: return launch_cells_t<double, 4, true>(p, sms, st, grid_out);
-      case 8: return launch_cells_t<double, 8, true>(p, sms, st, grid_out);
-      case 16: return launch_cells_t<double, 16, true>(p, sms, st, grid_out);
+      case 4: return launch_cells_t<double, 4, true>(p, sms, st, grid_out, launches);
+      case 8: return launch_cells_t<double, 8, true>(p, sms, st, grid_out, launches);
+      case 16: return launch_cells_t<double, 16, true>(p, sms, st, grid_out, launches);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (n) {
-    case 4: return launch_cells_t<double, 4, false>(p, sms, st, grid_out);
-    case 8: return launch_cells_t<double, 8, false>(p, sms, st, grid_out);
-    case 16: return launch_cells_t<double, 16, false>(p, sms, st, grid_out);
+    case 4: return launch_cells_t<double, 4, false>(p, sms, st, grid_out, launches);
+    case 8: return launch_cells_t<double, 8, false>(p, sms, st, grid_out, launches);
+    case 16: return launch_cells_t<double, 16, false>(p, sms, st, grid_out, launches);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -26,7 +26,8 @@ constexpr int cells_smem_bytes() {
 }
 
 template <typename T, int N, bool REPLACE>
-cudaError_t launch_cells_t(const CellKernelParams& p, int sms, cudaStream_t st, int* grid_out) {
+cudaError_t launch_cells_t(const CellKernelParams& p, int sms, cudaStream_t st, int* grid_out,
+                           int& launches) {
   constexpr int WPC = WorkerShape<N>::WPC, WORKERS = WorkerShape<N>::WORKERS;
   constexpr int threads = WPC * 32 * WORKERS;
   constexpr int smem = cells_smem_bytes<T, N>();
@@ -47,6 +48,7 @@ cudaError_t launch_cells_t(const CellKernelParams& p, int sms, cudaStream_t st, 
   }
   if (grid_out) *grid_out = grid;
   kern<<<grid, threads, smem, st>>>(p);
+  ++launches;
   return cudaGetLastError();
 }
 

@@ -1,8 +1,10 @@
 // eik_noalloc.cu -- eik_solve_device_noalloc: an FP64 solve that allocates
-// no memory at all, for callers that must not call cudaMalloc (code running
-// inside a CUDA-graph capture of another framework, a custom allocator that
-// owns all device memory, real-time paths where an allocation may block on
-// a device synchronisation, or sandboxes that forbid allocation calls).
+// no memory at all.  It serves callers that cannot call cudaMalloc during a
+// solve: programs whose own caching allocator has reserved the device memory
+// up front (a cudaMalloc would fail or force that allocator to release
+// blocks), latency-critical loops where an allocation can stall behind a
+// device-wide synchronisation, and plug-in code whose host framework only
+// lets it use memory handed to it.  The paper has no counterpart.
 //
 // The working memory of the solve lives in one file-scope device array of
 // fixed size, kNoallocScratchBytes.  Every device that loads the library
@@ -10,7 +12,7 @@
 // array's name as a device address (in host code it names a host-side
 // stand-in); the address is looked up once per device with
 // cudaGetSymbolAddress while that device is current, and passed to the
-// kernels from then on.
+// kernels from then on.  The call waits for its stream before it returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -111,6 +113,12 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   for (int a = 0; a < 3; ++a)
     if (dims[a] < 1 || dims[a] > (1 << 24)) return EIK_EINVAL;
   if (!(h > 0.0) || isinf(h) || !(tol >= 0.0) || isinf(tol)) return EIK_EINVAL;
+  // A grid needs more than 16 bytes of scratch per node (padded FP64 u and
+  // FP64 slowness), so anything above kNoallocScratchBytes / 16 nodes cannot
+  // fit.  This bound is checked before the node count is formed (the edges
+  // alone allow 2^72 nodes); every size below then stays far inside 64 bits.
+  if ((long long)dims[0] * dims[1] > (long long)(kNoallocScratchBytes / 16) / dims[2])
+    return EIK_EBUDGET;
   const int n = kNoallocCellN, n3 = n * n * n, np = 3 * (n - 1) + 1;
   const int nx = (int)dims[0], ny = (int)dims[1], nz = (int)dims[2];
   const int ncx = (nx + n - 1) / n, ncy = (ny + n - 1) / n, ncz = (nz + n - 1) / n;
@@ -274,8 +282,10 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   cells.lev_depth = nullptr;
   Control* dctl = reinterpret_cast<Control*>(A + off_ctl);
 
+  int launches = 0;
   CKN(launch_bulk_init(reinterpret_cast<const PrepInstance*>(A + off_prep), segs, (int)ncells,
-                       cells, dctl, reinterpret_cast<int*>(A + off_nsrc), true, n, 0.5, 0.0, st));
+                       cells, dctl, reinterpret_cast<int*>(A + off_nsrc), true, n, 0.5, 0.0, st,
+                       launches));
   CellKernelParams p;
   memset(&p, 0, sizeof(p));
   p.inst = reinterpret_cast<const Instance*>(A + off_instance);
@@ -294,9 +304,9 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.cell_key = 0;
   p.use_levels = 0;
   int grid = 0;
-  CKN(launch_cells(true, false, n, p, slot->sms, st, &grid));
+  CKN(launch_cells(true, false, n, p, slot->sms, st, &grid, launches));
   CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), segs, dctl,
-                              false, 0.0, st));
+                              false, 0.0, st, launches));
   CKN(cudaMemcpyAsync(&g_host_ctl, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   CKN(cudaStreamSynchronize(st));
 
@@ -311,7 +321,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
     stats->cell_n_used = n;
     stats->precision_used = EIK_FP64;
     memcpy(&stats->residual_max, &g_host_ctl.resid_bits, 8);
-    stats->kernel_launches = 8;
+    stats->kernel_launches = (uint64_t)launches;
     stats->grid_ctas = grid;
   }
   if (g_host_ctl.status) return g_host_ctl.status;

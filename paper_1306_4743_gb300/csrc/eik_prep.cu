@@ -727,8 +727,10 @@ static inline unsigned blocks_of(const Segments& g, int kind) {
 
 cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& g, int total_cells,
                              CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
-                             double width_factor, double kappa_rel, cudaStream_t st) {
+                             double width_factor, double kappa_rel, cudaStream_t st,
+                             int& launches) {
   const int c = g.count;
+  launches += 6;
   reset_cells_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells);
   minq_kernel<<<blocks_of(g, kSegRows), 256, 0, st>>>(d_pi, seg_of(g, kSegRows), c, ctl, n_src);
   if (fp64) {
@@ -747,8 +749,9 @@ cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& g, int to
 }
 
 cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& g, int total_cells,
-                               CellArrays cells, Control* ctl, cudaStream_t st) {
+                               CellArrays cells, Control* ctl, cudaStream_t st, int& launches) {
   const int c = g.count;
+  launches += cells.lev_depth ? 6 : 5;
   convert_u_kernel<<<blocks_of(g, kSegPad64), 256, 0, st>>>(d_pi, seg_of(g, kSegPad64), c, ctl);
   polish_keys_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells,
                                                               ctl, 0, 0.0);
@@ -764,8 +767,9 @@ cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& g, in
 
 cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi,
                                  const Segments& g, int total_cells, CellArrays cells,
-                                 Control* ctl, double kappa, cudaStream_t st) {
+                                 Control* ctl, double kappa, cudaStream_t st, int& launches) {
   const int c = g.count;
+  launches += 4;
   residual_extract_kernel<0><<<blocks_of(g, kSegRows), 256, 0, st>>>(d_fi, seg_of(g, kSegRows), c,
                                                                      ctl, kappa);
   polish_keys_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells,
@@ -777,8 +781,10 @@ cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance
 }
 
 cudaError_t launch_residual_extract(const FinalInstance* d_fi, const Segments& g, Control* ctl,
-                                    bool after_fallback, double kappa, cudaStream_t st) {
+                                    bool after_fallback, double kappa, cudaStream_t st,
+                                    int& launches) {
   const int c = g.count;
+  launches += 1;
   if (after_fallback)
     residual_extract_kernel<2><<<blocks_of(g, kSegRows), 256, 0, st>>>(d_fi, seg_of(g, kSegRows),
                                                                        c, ctl, kappa);

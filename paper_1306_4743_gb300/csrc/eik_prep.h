@@ -81,22 +81,25 @@ struct Segments {
 void make_segments(int count, const SegSizes* sizes, int* host_seg, int* totals);
 size_t segment_table_bytes(int count);
 
+// Every launcher adds the number of kernels it launched to `launches`.
 cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& seg, int total_cells,
                              CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
-                             double width_factor, double kappa_rel, cudaStream_t st);
+                             double width_factor, double kappa_rel, cudaStream_t st,
+                             int& launches);
 cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& seg, int total_cells,
-                               CellArrays cells, Control* ctl, cudaStream_t st);
+                               CellArrays cells, Control* ctl, cudaStream_t st, int& launches);
 cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi,
                                  const Segments& seg, int total_cells, CellArrays cells,
-                                 Control* ctl, double kappa, cudaStream_t st);
+                                 Control* ctl, double kappa, cudaStream_t st, int& launches);
 // after_fallback: the pass after the replace-mode fallback (a no-op on the
 // device unless it ran); otherwise the final pass of the FP64 path.
 cudaError_t launch_residual_extract(const FinalInstance* d_fi, const Segments& seg, Control* ctl,
-                                    bool after_fallback, double kappa, cudaStream_t st);
+                                    bool after_fallback, double kappa, cudaStream_t st,
+                                    int& launches);
 
 // Persistent cell kernels (eik_cells_f32.cu / eik_cells_f64.cu).
 cudaError_t launch_cells(bool fp64, bool replace, int n, const CellKernelParams& p, int sms,
-                         cudaStream_t st, int* grid_out);
+                         cudaStream_t st, int* grid_out, int& launches);
 
 // Shared memory bytes and threads of the cell kernel for (type, n).
 void cells_kernel_shape(bool fp64, int n, int* threads, int* smem_bytes, int* workers);

@@ -77,10 +77,12 @@ using eik::ServeState;
 using eik::Slot;
 using eik::kMaxBatch;
 
+// The same rule as the synchronous calls: each edge in [1, 2^24], at most
+// 2^34 nodes, bounded before the product is formed.
 bool dims_ok(const int64_t* d) {
   for (int a = 0; a < 3; ++a)
     if (d[a] < 1 || d[a] > (1 << 24)) return false;
-  return true;
+  return (long long)d[0] * d[1] <= (1ll << 34) / d[2];
 }
 
 void release_inputs(Request* r) {

@@ -37,6 +37,7 @@ struct Exec {
 // A launched batch, until eik_finish_batch has read it back.
 struct Launch {
   int count = 0, n = 0, grid = 0;
+  int launches = 0;  // kernels this batch enqueued
   bool polish = false, host_io = false, async_out = false;
   long long nodes_total = 0;
   Control* hres = nullptr;  // pinned copy of the control block

@@ -85,3 +85,21 @@ def test_binding_keeps_library_defaults():
     o = eik.make_opts(precision="fp64", cell_n=16, queue_order=0, bucket_width=2.0)
     assert (o.precision, o.cell_n, o.queue_order, o.bucket_width) == (0, 16, 0, 2.0)
     assert o.bulk_kappa_rel == d.bulk_kappa_rel and o.spin_cap_us == d.spin_cap_us
+
+
+def test_oversized_grids_rejected_before_any_product_overflows():
+    """Edges up to 2^24 each would give up to 2^72 nodes: the entry points
+    must bound the node count before forming it, and return before any
+    device call.  Dummy (non-null) pointers are never dereferenced."""
+    from paper_1306_4743_gb300 import eik
+    lib = eik.load()
+    dummy = ctypes.c_void_p(16)
+    for d in ((1 << 24, 1 << 24, 1 << 24), (1 << 24, 1 << 24, 2), (400, 400, 400),
+              (1 << 23, 1, 1)):
+        dims = (ctypes.c_int64 * 3)(*d)
+        rc = lib.eik_solve_device_noalloc(dims, 0.01, dummy, dummy, dummy, 0.0, dummy, None,
+                                          None)
+        assert rc == 3, (d, rc)  # EIK_EBUDGET: cannot fit the fixed scratch
+    dims = (ctypes.c_int64 * 3)(1 << 25, 1, 1)
+    assert lib.eik_solve_device_noalloc(dims, 0.01, dummy, dummy, dummy, 0.0, dummy, None,
+                                        None) == 1  # edge above 2^24: EIK_EINVAL

@@ -81,14 +81,16 @@ typedef struct {
                                in microseconds (default 5,000,000); 0 makes
                                every idle wait fail at once (test hook) */
   double bucket_width;      /* width of one queue bucket in units of
-                               (cell edge x mean slowness); <= 0 = default 0.25 */
+                               (cell edge x front slowness), the front
+                               slowness being the harmonic mean of s = h / F,
+                               h / mean(F); <= 0 = default 0.25 */
   int max_sweeps_per_visit; /* sweep limit of one cell visit (default 4096) */
   int queue_order;          /* 0 = strict: the next bucket starts once every
                                cell of the current one is finished;
                                1 = relaxed: once the current bucket is empty
                                (default) */
   double bulk_kappa_rel;    /* EIK_FP32_POLISH only: change threshold of the
-                               FP32 bulk sweeps, in units of (cell edge x mean
+                               FP32 bulk sweeps, in units of (cell edge x front
                                slowness) (default 1e-2).  Stopping the bulk
                                early leaves values high, never low, and the
                                FP64 polish starts above the fixed point, so

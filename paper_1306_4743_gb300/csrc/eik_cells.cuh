@@ -85,7 +85,7 @@ struct Geo {
   static constexpr int OFF_PERM = OFF_LIST + align128(N * N * 2);
   static constexpr int OFF_LOFF = OFF_PERM + PERM_BYTES;
   static constexpr int OFF_BAR = OFF_LOFF + LOFF_BYTES;
-  static constexpr int WORKER_BYTES = OFF_BAR + 128;
+  static constexpr int WORKER_BYTES = OFF_BAR + 256;
   // CTA-wide: plane table | plane offsets
   static constexpr int TAB_BYTES = align128(N3 * 2);
   static constexpr int OFFS_BYTES = align128((NPLANES + 1) * 4);
@@ -113,8 +113,10 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
 // its active bit, recompute it from its six neighbours (Eq. 2), store a
 // lower value (min mode) or any new value (replace mode), and on a change
 // by more than the threshold activate the neighbours that may now use it.
-// `left` records, per axis (bit 0 x, 1 y, 2 z), an activation on the plane
-// the sweep has just left.
+// `left` counts, per axis (bits 0-9 x, 10-19 y, 20-29 z), the activations of
+// neighbours on the plane the sweep has just left (at most one per node and
+// axis, and a thread takes at most 2 (3n - 2) nodes of a sweep, so a field
+// cannot overflow).
 template <typename T, int N, bool REPLACE>
 __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
                                             unsigned* __restrict__ chg, int si, int fx, int fy,
@@ -164,27 +166,27 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
       auto uses = [&](T y) { return REPLACE || vlt(nv, y); };
       if (i > 0 && uses(xm)) {
         activate(si - 1);
-        left |= fx == 0 ? 1u : 0u;
+        left += fx == 0 ? 1u : 0u;
       }
       if (i < N - 1 && uses(xp)) {
         activate(si + 1);
-        left |= fx != 0 ? 1u : 0u;
+        left += fx != 0 ? 1u : 0u;
       }
       if (j > 0 && uses(ym)) {
         activate(si - N);
-        left |= fy == 0 ? 2u : 0u;
+        left += fy == 0 ? (1u << 10) : 0u;
       }
       if (j < N - 1 && uses(yp)) {
         activate(si + N);
-        left |= fy != 0 ? 2u : 0u;
+        left += fy != 0 ? (1u << 10) : 0u;
       }
       if (k > 0 && uses(zm)) {
         activate(si - N * N);
-        left |= fz == 0 ? 4u : 0u;
+        left += fz == 0 ? (1u << 20) : 0u;
       }
       if (k < N - 1 && uses(zp)) {
         activate(si + N * N);
-        left |= fz != 0 ? 4u : 0u;
+        left += fz != 0 ? (1u << 20) : 0u;
       }
     }
   }
@@ -286,18 +288,35 @@ __device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restric
   }
 }
 
-// Worker-wide OR of the three axis bits.
+// Worker-wide sums of the three packed per-axis counts of left-behind
+// activations; returns the bit of the axis with the most (the lowest axis on
+// a tie), or 0 when no activation was left behind.  `ws` is 3 * WPC ints of
+// worker scratch.
 template <int WPC>
-__device__ __forceinline__ unsigned worker_or3(int worker, unsigned bits) {
-  if constexpr (WPC == 1) {
-    return __reduce_or_sync(0xffffffffu, bits);
-  } else {
-    unsigned r = 0;
-    if (bar_red_or(1 + worker, WPC * 32, (bits & 1u) != 0)) r |= 1u;
-    if (bar_red_or(1 + worker, WPC * 32, (bits & 2u) != 0)) r |= 2u;
-    if (bar_red_or(1 + worker, WPC * 32, (bits & 4u) != 0)) r |= 4u;
-    return r;
+__device__ __forceinline__ unsigned worker_most_left_axis(int worker, int tid, unsigned packed,
+                                                          int* ws) {
+  unsigned c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c[a] = __reduce_add_sync(0xffffffffu, (packed >> (10 * a)) & 1023u);
+  if constexpr (WPC > 1) {
+    if ((tid & 31) == 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) ws[3 * (tid >> 5) + a] = (int)c[a];
+    }
+    worker_sync<WPC>(worker);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      unsigned t = 0;
+#pragma unroll
+      for (int w = 0; w < WPC; ++w) t += (unsigned)ws[3 * w + a];
+      c[a] = t;
+    }
   }
+  if ((c[0] | c[1] | c[2]) == 0u) return 0u;
+  int best = 0;
+  if (c[1] > c[best]) best = 1;
+  if (c[2] > c[best]) best = 2;
+  return 1u << best;
 }
 
 // First and last plane (in the order of direction `dir`) that hold an
@@ -349,10 +368,11 @@ __device__ __forceinline__ void active_planes(const unsigned* __restrict__ chg, 
 // before and just after its own, so a node activated on the next plane is
 // swept later in this same sweep; past `last`, a plane with no active node
 // ends the sweep, as no later plane can hold one.  Returns (worker-wide)
-// the axes along which a node on the plane just left was activated: the
-// nodes still active afterwards.  With none, another sweep would change
-// nothing, so the cell has converged one sweep earlier than the plain
-// "until a sweep changes nothing" test would find.
+// the bit of the axis along which the most nodes on planes just left were
+// activated (those nodes are still active afterwards), or 0 when none was:
+// then another sweep would change nothing, so the cell has converged one
+// sweep earlier than the plain "until a sweep changes nothing" test would
+// find.  The next sweep reverses that one axis.
 //
 // COMPACT (one-warp workers): the active nodes of each plane are first
 // gathered into a list by ballot and the lanes then take list entries, so
@@ -366,7 +386,7 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
                                                const int* __restrict__ off,
                                                unsigned short* __restrict__ list, int dir,
                                                int first, int last, int tid, int worker,
-                                               T kappa, unsigned& n_updates) {
+                                               T kappa, unsigned& n_updates, int* ws) {
   using G = Geo<T, N>;
   constexpr int NT = WPC * 32;
   // Nodes of one plane do not depend on each other: a thread takes up to UNR
@@ -440,7 +460,7 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
     }
     if (!any && C >= last) break;
   }
-  return worker_or3<WPC>(worker, left);
+  return worker_most_left_axis<WPC>(worker, tid, left, ws);
 }
 
 template <typename T, int N, int WPC, int WORKERS, bool REPLACE>
@@ -466,7 +486,8 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
   T* S = reinterpret_cast<T*>(wbase + G::OFF_S);
   unsigned* chg = reinterpret_cast<unsigned*>(wbase + G::OFF_CHG);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(wbase + G::OFF_BAR);
-  // scratch: [0] cell, [1] direction word, [2..7] face keys, [12..19] plane range
+  // scratch: [0] cell, [1] direction word, [2..7] face keys, [12..23] plane
+  // range, [32..49] per-axis counts of left-behind activations
   int* wshared = reinterpret_cast<int*>(wbase + G::OFF_BAR + 16);
   unsigned short* list = reinterpret_cast<unsigned short*>(wbase + G::OFF_LIST);
   constexpr bool COMPACT = sizeof(T) == 8 && WPC == 1;
@@ -630,8 +651,11 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     // Min mode: first the direction that leaves the lower halo face behind
     // on each axis (the cell's inflow side; upward on an axis without halo
     // values) if it is a preferred direction, else the first preferred one
-    // (in the standard order); then each next sweep reverses the axes along
-    // which the last one left active nodes behind.  Replace mode: every
+    // (in the standard order); then each next sweep reverses the one axis
+    // along which the last one left the most active nodes behind (reversing
+    // every such axis took more sweeps: a CPU model of first visits of 16^3
+    // cells gave 3.5 against 2.9 sweeps on the 257^3 oscillatory field and
+    // 13.9 against 8.6 on a 129^3 barrier field).  Replace mode: every
     // preferred direction, then the standard loop.  A sweep
     // covers only the planes from the first one holding an active node.
     int nsw = 0;
@@ -661,7 +685,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
         return;
       }
       lm = sweep_cell<T, N, WPC, REPLACE, COMPACT>(U, S, chg, tab, off, list, d, first, last, tid,
-                                                   worker, kappa, n_updates);
+                                                   worker, kappa, n_updates, wshared + 32);
       ++nsw;
     };
     if constexpr (!REPLACE) {

@@ -510,10 +510,95 @@ __device__ __forceinline__ int scan_next_bucket(const CellArrays& c, unsigned cu
   return kNumBuckets;
 }
 
+// Warp-collective attempt to take a cell from bucket `b` (absolute index):
+// the lanes read the bucket's 32 sub-stack heads at once and pop from the
+// first non-empty one at or after the warp's own starting sub-stack.
+// Returns the cell, now RUNNING, or -1 if every sub-stack was empty or every
+// pop lost its race; *stop is set on a queue inconsistency (status set).
+// The bucket's run count is raised before the pop (so a strict-order
+// advance waits for it) and stays raised for a taken cell until it retires.
+__device__ __forceinline__ int try_pop_bucket(const CellArrays& c, Control* ctl, unsigned b,
+                                              unsigned sub, int lane, unsigned* slot_out,
+                                              int* stop) {
+  const unsigned slot = b & kBucketMask;
+  unsigned long long* head = sub_head(c, slot, sub);
+  const unsigned long long h = ld_acquire_u64(head);
+  unsigned ne = __ballot_sync(0xffffffffu, (h & 0xffffffffull) != 0ull);
+  if (!ne) return -1;
+  if (lane == 0) atomicAdd(c.run + slot, 1);  // reserve before taking: blocks an advance
+  __syncwarp();
+  int cell = -1;
+  while (ne) {
+    const int l = __ffs(ne) - 1;
+    int got = -1;
+    if (lane == l) got = stack_pop(head, c, h);
+    got = __shfl_sync(0xffffffffu, got, l);
+    if (got >= 0) {
+      cell = got;
+      break;
+    }
+    ne &= ne - 1u;
+  }
+  int bad = 0;
+  if (lane == 0) {
+    if (cell < 0) {
+      atomicSub(c.run + slot, 1);
+    } else {
+      atomicSub(c.cnt + slot, 1);
+      atomicSub(&ctl->queued, 1);
+      // QUEUED -> RUNNING (drops DIRTY: this visit loads the newest data)
+      unsigned st = ld_relaxed_u32(c.state + cell);
+      for (;;) {
+        if (!(st & kStQueued)) {
+          set_status(ctl, EIK_EQUEUE);
+          bad = 1;
+          break;
+        }
+        const unsigned prev = atomicCAS(c.state + cell, st, kStRunning);
+        if (prev == st) break;
+        st = prev;
+      }
+      __threadfence();
+      *slot_out = slot;
+    }
+  }
+  bad = __shfl_sync(0xffffffffu, bad, 0);
+  if (bad) {
+    *stop = 1;
+    return -1;
+  }
+  return __shfl_sync(0xffffffffu, cell, 0);
+}
+
+// Move `cur` from `from` to `to` (> from) if no other worker moved it, then
+// pull it back to any bucket in between that a racing push filled.
+// Lane 0 only.
+__device__ __forceinline__ void advance_cur(const CellArrays& c, Control* ctl, unsigned from,
+                                            unsigned to) {
+  if (atomicCAS(&ctl->cur, from, to) == from) {
+    __threadfence();
+    for (unsigned o = from; o < to; ++o) {
+      if (!bucket_empty(c, o & kBucketMask)) {
+        atomicMin(&ctl->cur, o);
+        break;
+      }
+    }
+  }
+}
+
 // Warp-collective pop (all 32 lanes of the calling warp).  Returns a cell
 // whose state is now RUNNING (and the ring slot it came from in *slot_out),
 // or -1 when the solve is finished or failed.  `rot` picks the sub-stack the
 // warp tries first.
+//
+// Relaxed order takes a cell from the lowest non-empty bucket: when bucket
+// `cur` has nothing to take, the warp looks at once at the bucket counts
+// ahead of it and pops from the first non-empty bucket, moving `cur` there
+// if bucket `cur` is empty.  (Waiting for `cur` to advance before looking
+// further left most workers idle while thousands of cells sat in the next
+// few buckets: pushes of revisited cells keep pulling `cur` back.)  Strict
+// order takes cells from bucket `cur` only, and moves on once none taken
+// from it is still running.
 static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
                                      unsigned long long spin_cap_ns, int lane,
                                      unsigned* slot_out, bool relaxed, unsigned rot) {
@@ -523,12 +608,10 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
   unsigned polls = 0;
   const unsigned sub = (lane + rot) & (kSubStacks - 1);
   for (;;) {
-    int stop = 0, cell = -1, can_advance = 0;
+    int stop = 0, can_advance = 0;
     unsigned cur = 0;
-    // The fast path of a poll reads cur and the sub-stack heads of its
-    // bucket; termination, errors and bucket completion are checked every
-    // 4th empty poll, to keep the traffic of waiting workers on the shared
-    // control words low.
+    // Termination and errors are checked every 4th poll, to keep the
+    // traffic of waiting workers on the shared control words low.
     const bool full_check = (polls & 3u) == 0u;
     if (lane == 0) {
       if (full_check)
@@ -539,59 +622,31 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
     if (stop) return -1;
     cur = __shfl_sync(0xffffffffu, cur, 0);
     const unsigned slot = cur & kBucketMask;
-    unsigned long long* head = sub_head(c, slot, sub);
-    const unsigned long long h = ld_acquire_u64(head);
-    unsigned ne = __ballot_sync(0xffffffffu, (h & 0xffffffffull) != 0ull);
-    if (ne) {
-      if (lane == 0) atomicAdd(c.run + slot, 1);  // reserve before taking: blocks an advance
-      __syncwarp();
-      while (ne) {
-        const int l = __ffs(ne) - 1;
-        int got = -1;
-        if (lane == l) got = stack_pop(head, c, h);
-        got = __shfl_sync(0xffffffffu, got, l);
-        if (got >= 0) {
-          cell = got;
-          break;
-        }
-        ne &= ne - 1u;
+    int cell = try_pop_bucket(c, ctl, cur, sub, lane, slot_out, &stop);
+    if (stop) return -1;
+    if (cell >= 0) return cell;
+    ++polls;
+    if (relaxed) {
+      // the lowest non-empty bucket within 128 ahead of `cur`
+      const int found = scan_next_bucket(c, cur, false, lane);
+      if (found < kNumBuckets) {
+        const unsigned b = cur + (unsigned)found;
+        if (lane == 0 && bucket_empty(c, slot)) advance_cur(c, ctl, cur, b);
+        __syncwarp();
+        cell = try_pop_bucket(c, ctl, b, sub, lane, slot_out, &stop);
+        if (stop) return -1;
+        if (cell >= 0) return cell;
+        // lost every race, or caught a push or pop between its count and
+        // its link: look again after the shortest wait (which still runs
+        // the no-progress watchdog below)
+        backoff = 64;
       }
-      if (lane == 0) {
-        if (cell < 0) {
-          atomicSub(c.run + slot, 1);
-        } else {
-          atomicSub(c.cnt + slot, 1);
-          atomicSub(&ctl->queued, 1);
-          // QUEUED -> RUNNING (drops DIRTY: this visit loads the newest data)
-          unsigned st = ld_relaxed_u32(c.state + cell);
-          for (;;) {
-            if (!(st & kStQueued)) {
-              set_status(ctl, EIK_EQUEUE);
-              cell = -1;
-              stop = 1;
-              break;
-            }
-            const unsigned prev = atomicCAS(c.state + cell, st, kStRunning);
-            if (prev == st) break;
-            st = prev;
-          }
-          __threadfence();
-          *slot_out = slot;
-        }
-      }
-      stop = __shfl_sync(0xffffffffu, stop, 0);
-      if (stop) return -1;
-      cell = __shfl_sync(0xffffffffu, cell, 0);
-      if (cell >= 0) return cell;
-      ++polls;
-      continue;  // lost every race: look again at once
     }
     if (lane == 0 && full_check) {
       // strict order: the bucket is done when no cell taken from it is
       // still running; relaxed order: as soon as it is empty
       can_advance = (relaxed || ld_acquire_s32(c.run + slot) == 0) && bucket_empty(c, slot);
     }
-    ++polls;
     can_advance = __shfl_sync(0xffffffffu, can_advance, 0);
 
     if (can_advance) {
@@ -603,17 +658,7 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
         int found = scan_next_bucket(c, cur, false, lane);
         if (found == kNumBuckets) found = scan_next_bucket(c, cur, true, lane);
         if (found < kNumBuckets) {
-          if (lane == 0) {
-            if (atomicCAS(&ctl->cur, cur, cur + (unsigned)found) == cur) {
-              __threadfence();
-              for (int o = 0; o < found; ++o) {
-                if (!bucket_empty(c, (cur + (unsigned)o) & kBucketMask)) {
-                  atomicMin(&ctl->cur, cur + (unsigned)o);
-                  break;
-                }
-              }
-            }
-          }
+          if (lane == 0) advance_cur(c, ctl, cur, cur + (unsigned)found);
           __syncwarp();
           backoff = 64;
           continue;

@@ -85,8 +85,8 @@ struct Control {
   float inv_width;            // 1 / bucket width
   int n_sources;              // exit nodes seen by the init kernel
   int bad_input;              // an input failed validation
-  double sum_s;               // sum of s over non-exit nodes (bucket width estimate)
-  unsigned long long n_s;     // number of terms in sum_s
+  double sum_inv_s;           // sum of 1 / s = F / h over non-exit nodes
+  unsigned long long n_s;     // number of terms in sum_inv_s
   unsigned long long min_q_ord;    // ordered bits of min q (double)
   unsigned long long umax_bits;    // ordered bits of the largest finite u
                                    // (of the lifted start, during the polish)

@@ -206,7 +206,8 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __
   const int ey = N * P.ncy, ex = N * P.ncx;  // extents covered by the cells
   const long long rows = (long long)ey * N * P.ncz;
   const double qb = q_base(ctl);
-  float acc = 0.0f;  // for the mean of s (bucket width): FP32 is plenty
+  const float inv_h = (float)(1.0 / P.h);
+  float acc = 0.0f;  // sum of 1 / s = F / h (bucket width): FP32 is plenty
   unsigned long long cnt = 0;
   int bad = 0;
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -232,7 +233,7 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __
             bad = 1;
           } else {
             sv = slowness(P.h, f);
-            acc += f32_of_f64_nn(sv);
+            acc += f * inv_h;
             ++cnt;
           }
         }
@@ -247,7 +248,7 @@ __global__ void init_s_kernel(const PrepInstance* __restrict__ pi, const int* __
   bad = block_reduce(bad, MaxOp());
   if (threadIdx.x == 0) {
     if (cnt) {
-      atomicAdd(&ctl->sum_s, (double)acc);
+      atomicAdd(&ctl->sum_inv_s, (double)acc);
       atomicAdd(&ctl->n_s, cnt);
     }
     if (bad) atomicExch(&ctl->bad_input, 1);
@@ -265,8 +266,12 @@ __global__ void setup_bulk_kernel(Control* ctl, const int* n_src, int count, int
     set_status(ctl, EIK_EINVAL);
     return;
   }
-  const double mean_s = ctl->n_s ? ctl->sum_s / (double)ctl->n_s : 1.0;
-  double width = width_factor * (double)n * mean_s;
+  // The slowness the front advances at: the harmonic mean of s, h / mean(F).
+  // (The arithmetic mean is dominated by the slowest nodes: on a field with
+  // 30% of its nodes at F = 0.01 it is ~30 h, and buckets that wide let cells
+  // far ahead of the front in the fast regions start early and be revisited.)
+  const double s_front = ctl->sum_inv_s > 0.0 ? (double)ctl->n_s / ctl->sum_inv_s : 1.0;
+  double width = width_factor * (double)n * s_front;
   if (!(width > 0.0) || !isfinite(width)) width = 1.0;
   ctl->base = 0.0f;  // values are stored relative to q_min
   ctl->inv_width = (float)(1.0 / width);
@@ -274,7 +279,7 @@ __global__ void setup_bulk_kernel(Control* ctl, const int* n_src, int count, int
   // changes of a few FP32 ulps of a value one cell away from the exit set
   // (stopping early only leaves values high; the polish starts above the
   // fixed point either way)
-  ctl->kappa_bulk = kappa_rel * (double)n * mean_s;
+  ctl->kappa_bulk = kappa_rel * (double)n * s_front;
   ctl->cur = 0u;
   ctl->active = 0;
   ctl->queued = 0;

@@ -435,8 +435,9 @@ def run_ours(args):
     world, rank, local = dist_setup()
     jobs = None
     rec, edge = headline(args)
-    if rank == 0 and not args.no_cpu_baseline:
-        # spawned before this process makes any CUDA call
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle legs run at N = 1 only; spawned before this process
+        # makes any CUDA call
         jobs = OracleJobs(args.oracle_jobs)
         head_key = jobs.submit(rec, edge)
         if not args.no_extras:

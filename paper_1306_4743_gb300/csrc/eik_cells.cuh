@@ -433,7 +433,15 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
         did = true;
         update_node<T, N, REPLACE>(U, S, chg, (int)cur[h], fx, fy, fz, kappa, n_updates, left);
       }
-      any = worker_any<WPC>(worker, did);  // also ends the plane
+      // also ends the plane; before the last initially active plane the
+      // sweep cannot end, so a plain barrier does (bar.sync costs about half
+      // a bar.red.or)
+      if (C < last) {
+        worker_sync<WPC>(worker);
+        any = true;
+      } else {
+        any = worker_any<WPC>(worker, did);
+      }
     } else {
       // gather the plane's active nodes
       const int lane = tid & 31;

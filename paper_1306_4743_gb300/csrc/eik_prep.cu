@@ -102,19 +102,33 @@ __global__ void minq_kernel(const PrepInstance* __restrict__ pi, const int* __re
   const long long rows = (long long)P.ny * P.nz;
   unsigned long long minq = ~0ull;
   int nsrc = 0, bad = 0;
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (long long r = w.first + (threadIdx.x >> 5); r < w.first + kRowsPerBlock && r < rows;
-       r += nw) {
-    const long long base = r * P.nx;
-    for (int i = lane; i < P.nx; i += 32) {
-      if (P.mask[base + i]) {
-        const double qv = P.q[base + i];
-        if (!isfinite(qv)) bad = 1;
-        ++nsrc;
-        const unsigned long long o = ord_of_double(qv);
-        minq = o < minq ? o : minq;
-      }
-    }
+  // the block's rows are one contiguous run of mask bytes [lo, hi): read it
+  // in 16-byte words where aligned (exit nodes are rare, so almost every
+  // word is zero and the pass is this read), bytes at the two ends
+  const long long lo = w.first * P.nx;
+  const long long hi = (w.first + kRowsPerBlock < rows ? w.first + kRowsPerBlock : rows) * P.nx;
+  auto take = [&](long long e) {
+    const double qv = P.q[e];
+    if (!isfinite(qv)) bad = 1;
+    ++nsrc;
+    const unsigned long long o = ord_of_double(qv);
+    minq = o < minq ? o : minq;
+  };
+  const uintptr_t base = reinterpret_cast<uintptr_t>(P.mask);
+  long long a0 = lo + (long long)((16u - ((base + (uintptr_t)lo) & 15u)) & 15u);
+  if (a0 > hi) a0 = hi;
+  long long a1 = a0 + ((hi - a0) & ~15ll);
+  for (long long e = lo + threadIdx.x; e < a0; e += blockDim.x)
+    if (P.mask[e]) take(e);
+  for (long long e = a1 + threadIdx.x; e < hi; e += blockDim.x)
+    if (P.mask[e]) take(e);
+  const uint4* m4 = reinterpret_cast<const uint4*>(P.mask + a0);
+  const long long nv = (a1 - a0) >> 4;
+  for (long long v = threadIdx.x; v < nv; v += blockDim.x) {
+    const uint4 m = __ldg(m4 + v);
+    if ((m.x | m.y | m.z | m.w) == 0u) continue;
+    for (int t = 0; t < 16; ++t)
+      if (P.mask[a0 + 16 * v + t]) take(a0 + 16 * v + t);
   }
   nsrc = block_reduce(nsrc, SumOp());
   bad = block_reduce(bad, MaxOp());
@@ -319,28 +333,46 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, const in
     const long long lrow = inside ? (long long)P.nx * ((y - 1) + (long long)P.ny * (z - 1)) : 0;
     const float* row32 = u32 + r * P.px32;
     double* row64 = u64 + r * P.px64;
-    for (int x = lane; x < P.px64; x += 32) {
-      double v = CUDART_INF;
-      if (inside && x >= 1 && x <= P.nx) {
-        const long long lin = lrow + x - 1;
-        if (P.mask[lin]) {
-          v = P.q[lin] - qb;
-        } else {
-          // Lift the FP32 value above the FP64 fixed point: its rounding
-          // error grows at most ~2^-24 u per node along a characteristic (u
-          // is stored relative to q_min), so a lift of 2^-11 u covers paths
-          // of up to 2^13 nodes.  The monotone FP64 sweeps then descend to
-          // the fixed point.  The lift is formed in FP32 (its own rounding,
-          // 2^-24 u, is far inside the margin) and widened on the integer
-          // pipe: no FP64 instruction per node.
-          v = f64_of_f32_nn(row32[x] * 1.00048828125f);
-        }
-        if (isfinite(v)) {
-          const unsigned long long o = ord_of_double(v);
-          mx = o > mx ? o : mx;
+    constexpr int R = 4;  // loads of R nodes per lane in flight at once
+    for (int x0 = lane; x0 < P.px64; x0 += 32 * R) {
+      unsigned char mk[R];
+      float w32[R];
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        const int x = x0 + 32 * h;
+        mk[h] = 0;
+        w32[h] = 0.0f;
+        if (inside && x >= 1 && x <= P.nx) {
+          mk[h] = __ldg(P.mask + lrow + x - 1);
+          w32[h] = __ldg(row32 + x);
         }
       }
-      row64[x] = v;
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        const int x = x0 + 32 * h;
+        if (x >= P.px64) break;
+        double v = CUDART_INF;
+        if (inside && x >= 1 && x <= P.nx) {
+          const long long lin = lrow + x - 1;
+          if (mk[h]) {
+            v = P.q[lin] - qb;
+          } else {
+            // Lift the FP32 value above the FP64 fixed point: its rounding
+            // error grows at most ~2^-24 u per node along a characteristic (u
+            // is stored relative to q_min), so a lift of 2^-11 u covers paths
+            // of up to 2^13 nodes.  The monotone FP64 sweeps then descend to
+            // the fixed point.  The lift is formed in FP32 (its own rounding,
+            // 2^-24 u, is far inside the margin) and widened on the integer
+            // pipe: no FP64 instruction per node.
+            v = f64_of_f32_nn(w32[h] * 1.00048828125f);
+          }
+          if (isfinite(v)) {
+            const unsigned long long o = ord_of_double(v);
+            mx = o > mx ? o : mx;
+          }
+        }
+        row64[x] = v;
+      }
     }
   }
   block_max_u64(mx, &ctl->umax_bits);

@@ -111,6 +111,16 @@ typedef struct {
                                  request); 0 = default 64 M.  Smaller batches
                                  start sooner, larger ones use the device
                                  better. */
+  double polish_lift;       /* EIK_FP32_POLISH only: the FP32 result is raised
+                               by this fraction of itself before the monotone
+                               FP64 polish, so that the polish starts above the
+                               fixed point (FP32 rounding grows ~2^-24 u per
+                               node along a characteristic); 0 = default 2^-11.
+                               A negative value starts below the fixed point,
+                               where monotone sweeps cannot arrive: the
+                               residual check then sends every cell to the
+                               replace-mode polish (fallback_used = 1), which
+                               is how that path is tested. */
 } eik_opts;
 
 /* Counters and results of one solve (of the whole batch for batch calls). */

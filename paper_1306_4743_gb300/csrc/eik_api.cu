@@ -564,8 +564,9 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas, nl));
   CK(cudaEventRecord(ex.ev[2], st));
   if (polish) {
+    const float lift = ctx->opts.polish_lift != 0.0 ? (float)ctx->opts.polish_lift : 0x1p-11f;
     CK(launch_polish_prep(reinterpret_cast<const PolishInstance*>(A + L.off_pol), segs,
-                          L.total_cells, cells, dctl, st, nl));
+                          L.total_cells, cells, dctl, lift, st, nl));
     p.inst = reinterpret_cast<const Instance*>(A + L.off_inst64);
     p.tmaps = reinterpret_cast<const CUtensorMap*>(A + L.off_tmap64);
     p.pass = 1;
@@ -804,6 +805,7 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
     return EIK_EINVAL;
   if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
   if (!(o.bulk_kappa_rel >= 0.0) || isinf(o.bulk_kappa_rel)) return EIK_EINVAL;
+  if (!(o.polish_lift > -0.5 && o.polish_lift < 1.0)) return EIK_EINVAL;
   if (!(o.bucket_width > 0.0)) o.bucket_width = 0.25;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {

@@ -317,7 +317,7 @@ __global__ void seed_sources_kernel(int total_cells, CellArrays c, Control* ctl,
 
 // FP32 result -> FP64 padded array of the polish; largest finite value.
 __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, const int* __restrict__ seg,
-                                 int count, Control* ctl) {
+                                 int count, Control* ctl, float lift) {
   const BlockWork w = block_work(seg, count, kRowsPerBlock);
   const PolishInstance P = pi[w.inst];
   const double qb = q_base(ctl);
@@ -359,12 +359,12 @@ __global__ void convert_u_kernel(const PolishInstance* __restrict__ pi, const in
           } else {
             // Lift the FP32 value above the FP64 fixed point: its rounding
             // error grows at most ~2^-24 u per node along a characteristic (u
-            // is stored relative to q_min), so a lift of 2^-11 u covers paths
-            // of up to 2^13 nodes.  The monotone FP64 sweeps then descend to
-            // the fixed point.  The lift is formed in FP32 (its own rounding,
-            // 2^-24 u, is far inside the margin) and widened on the integer
-            // pipe: no FP64 instruction per node.
-            v = f64_of_f32_nn(w32[h] * 1.00048828125f);
+            // is stored relative to q_min), so the default lift of 2^-11 u
+            // covers paths of up to 2^13 nodes.  The monotone FP64 sweeps
+            // then descend to the fixed point.  The lift is formed in FP32
+            // (its own rounding, 2^-24 u, is far inside the margin) and
+            // widened on the integer pipe: no FP64 instruction per node.
+            v = f64_of_f32_nn(w32[h] * lift);
           }
           if (isfinite(v)) {
             const unsigned long long o = ord_of_double(v);
@@ -786,10 +786,12 @@ cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& g, int to
 }
 
 cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& g, int total_cells,
-                               CellArrays cells, Control* ctl, cudaStream_t st, int& launches) {
+                               CellArrays cells, Control* ctl, float lift, cudaStream_t st,
+                               int& launches) {
   const int c = g.count;
   launches += cells.lev_depth ? 6 : 5;
-  convert_u_kernel<<<blocks_of(g, kSegPad64), 256, 0, st>>>(d_pi, seg_of(g, kSegPad64), c, ctl);
+  convert_u_kernel<<<blocks_of(g, kSegPad64), 256, 0, st>>>(d_pi, seg_of(g, kSegPad64), c, ctl,
+                                                             1.0f + lift);
   polish_keys_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c, cells,
                                                               ctl, 0, 0.0);
   polish_graph_kernel<<<blocks_of(g, kSegCells), 256, 0, st>>>(d_pi, seg_of(g, kSegCells), c,

@@ -86,8 +86,11 @@ cudaError_t launch_bulk_init(const PrepInstance* d_pi, const Segments& seg, int 
                              CellArrays cells, Control* ctl, int* n_src, bool fp64, int n,
                              double width_factor, double kappa_rel, cudaStream_t st,
                              int& launches);
+// lift: the FP32 result is raised by this fraction of itself (see
+// eik_opts.polish_lift) on its way to the FP64 polish array.
 cudaError_t launch_polish_prep(const PolishInstance* d_pi, const Segments& seg, int total_cells,
-                               CellArrays cells, Control* ctl, cudaStream_t st, int& launches);
+                               CellArrays cells, Control* ctl, float lift, cudaStream_t st,
+                               int& launches);
 cudaError_t launch_fallback_prep(const PolishInstance* d_pi, const FinalInstance* d_fi,
                                  const Segments& seg, int total_cells, CellArrays cells,
                                  Control* ctl, double kappa, cudaStream_t st, int& launches);

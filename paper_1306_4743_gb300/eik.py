@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("queue_order", ctypes.c_int),
                 ("bulk_kappa_rel", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("cell_key", ctypes.c_int),
-                ("reserved4", ctypes.c_int), ("serve_batch_nodes", ctypes.c_uint64)]
+                ("reserved4", ctypes.c_int), ("serve_batch_nodes", ctypes.c_uint64),
+                ("polish_lift", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -175,7 +176,7 @@ def default_opts() -> Opts:
 def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
               spin_cap_us=None, bucket_width=None, max_sweeps_per_visit=None, max_ctas=0,
               bulk_kappa_rel=None, queue_order=None, use_graphs=None,
-              cell_key=None, serve_batch_nodes=None) -> Opts:
+              cell_key=None, serve_batch_nodes=None, polish_lift=None) -> Opts:
     """eik_opts from the library defaults with the given fields changed
     (None = keep the default)."""
     o = default_opts()
@@ -200,6 +201,8 @@ def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
         o.cell_key = int(cell_key)
     if serve_batch_nodes is not None:
         o.serve_batch_nodes = int(serve_batch_nodes)
+    if polish_lift is not None:
+        o.polish_lift = float(polish_lift)
     return o
 
 
@@ -229,7 +232,8 @@ class Solver:
     def __init__(self, precision="fp32_polish", cell_n=0, device=0,
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
                  max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
-                 queue_order=None, use_graphs=None, cell_key=None, serve_batch_nodes=None):
+                 queue_order=None, use_graphs=None, cell_key=None, serve_batch_nodes=None,
+                 polish_lift=None):
         """Options left at None keep the library defaults (eik_opts_default)."""
         self.lib = load()
         o = make_opts(precision=precision, cell_n=cell_n, device=device,
@@ -237,7 +241,7 @@ class Solver:
                       bucket_width=bucket_width, max_sweeps_per_visit=max_sweeps_per_visit,
                       max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
                       queue_order=queue_order, use_graphs=use_graphs, cell_key=cell_key,
-                      serve_batch_nodes=serve_batch_nodes)
+                      serve_batch_nodes=serve_batch_nodes, polish_lift=polish_lift)
         self.opts = o
         self._outputs = {}  # ticket -> output array, alive until done or cancelled
         self.ctx = ctypes.c_void_p()

@@ -93,3 +93,146 @@ def test_two_gloo_ranks_agree_on_the_split():
     assert sorted(shards[0] + shards[1]) == list(range(len(sizes)))
     assert shards == dispatch.partition(sizes, 2)
     assert sum(c[1] for c in counts) == sum(sizes)
+
+
+# --- serving across GPUs ------------------------------------------------------
+def _serving_sizes(n=120):
+    return [e ** 3 for (_, e, _) in W.serving_requests(n=n, rate=1.0, seed=5)]
+
+
+def test_assign_online_is_greedy_least_loaded_and_deterministic():
+    sizes = _serving_sizes()
+    for world in (1, 2, 3, 4):
+        a = dispatch.assign_online(sizes, world)
+        assert a == dispatch.assign_online(sizes, world)
+        assert len(a) == len(sizes) and set(a) <= set(range(world))
+        loads = [sum(s for s, r in zip(sizes, a) if r == k) for k in range(world)]
+        assert max(loads) - min(loads) <= max(sizes)
+    # each request went to a rank that was least loaded when it arrived
+    load = [0, 0, 0]
+    for s, r in zip(sizes, dispatch.assign_online(sizes, 3)):
+        assert load[r] == min(load)
+        load[r] += s
+
+
+def test_assign_online_respects_budgets():
+    sizes = [100, 10, 100, 10]
+    a = dispatch.assign_online(sizes, 2, budgets=[1e9, 50 * 37.0])
+    assert a[0] == 0 and a[2] == 0  # the large requests fit rank 0 only
+    with pytest.raises(ValueError):
+        dispatch.assign_online([1000], 2, budgets=[10.0, 10.0])
+
+
+class _FakeServer:
+    """Stands in for eik.Solver's submit / poll on CPU: a request completes
+    after a number of polls that grows with its size, and its 'solution' is
+    h, so the caller can tell which request it got."""
+
+    def __init__(self, name):
+        self.name = name
+        self.req = {}
+        self.next = 1
+        self.closed = False
+
+    def submit(self, F, mask, q, h, tol=0.0, out=None):
+        t = self.next
+        self.next += 1
+        u = np.full(F.shape, float(h)) if out is None else out
+        self.req[t] = [max(1, F.size // 4000), u]
+        return t, u
+
+    def poll(self, t):
+        r = self.req[t]
+        r[0] -= 1
+        if r[0] <= 0:
+            del self.req[t]
+            return True, 0, {"server": self.name}
+        return False, 0, {}
+
+    def cancel(self, t):
+        return 0 if self.req.pop(t, None) is not None else 9
+
+    def close(self):
+        self.closed = True
+
+
+def _requests(n=40):
+    out = []
+    for k, (_, e, _) in enumerate(W.serving_requests(n=n, rate=1.0, seed=5)):
+        e = max(3, e // 8)  # small stand-ins of the same size mix
+        out.append((np.zeros((e, e, e), np.float32), None, None, float(k)))
+    return out
+
+
+def test_sharded_server_balances_outstanding_nodes_and_completes_all():
+    reqs = _requests()
+    backs = [_FakeServer(i) for i in range(3)]
+    srv = dispatch.ShardedServer(backs)
+    tickets = {}
+    for k, (F, m, q, h) in enumerate(reqs):
+        before = list(srv.outstanding)
+        t, u = srv.submit(F, m, q, h)
+        r = srv.tickets[t][0]
+        assert before[r] == min(before)  # least outstanding nodes at submission
+        tickets[t] = k
+    seen = {}
+    while tickets:
+        for t in list(tickets):
+            done, rc, st = srv.poll(t)
+            if done:
+                k = tickets.pop(t)
+                assert rc == 0 and st["backend"] == st["server"]
+                seen[k] = st["backend"]
+    assert sorted(seen) == list(range(len(reqs)))
+    assert srv.outstanding == [0, 0, 0] and len(set(seen.values())) == 3
+    srv.close()
+    assert all(b.closed for b in backs)
+
+
+def test_sharded_server_cancel_and_budget():
+    srv = dispatch.ShardedServer([_FakeServer(0), _FakeServer(1)], budgets=[1e12, 8 * 37.0])
+    F = np.zeros((4, 4, 4), np.float32)
+    t, _ = srv.submit(F, None, None, 1.0)
+    assert srv.tickets[t][0] == 0  # 64 nodes do not fit backend 1's budget of 8
+    assert srv.cancel(t) == 0 and srv.outstanding == [0, 0]
+    with pytest.raises(ValueError):
+        dispatch.ShardedServer([_FakeServer(0)], budgets=[1.0]).submit(F, None, None, 1.0)
+
+
+def _serve_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    reqs = _requests()
+    done = dispatch.serve_sharded(_FakeServer(rank), reqs, rank, world)
+    # check only: which requests this rank served, and that each got its own
+    # answer back (the split itself took no collective)
+    mine = torch.full((len(reqs),), -1, dtype=torch.int64)
+    for k, (u, rc) in done.items():
+        assert rc == 0 and float(u.flat[0]) == float(k)
+        mine[k] = rank
+    allm = [torch.zeros(len(reqs), dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(allm, mine)
+    dist.destroy_process_group()
+    if rank == 0:
+        q.put([a.tolist() for a in allm])
+
+
+def test_two_gloo_ranks_serve_disjoint_covering_shares():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_serve_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    allm = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    reqs = _requests()
+    owner = dispatch.assign_online([r[0].size for r in reqs], 2)
+    for k in range(len(reqs)):
+        served = [r for r in range(2) if allm[r][k] == r]
+        assert served == [owner[k]], k

@@ -686,7 +686,9 @@ def run_extras(args, eik, W, torch, np, dev, local, rank, world, flush, jobs, ba
             bn, bc = s2.autotune(p2.F, p2.mask, p2.q, p2.h, tol=tol)
             s2.solve(*d2, p2.h, tol=tol, out=u2)
             _, ts, sts = time_solves(s2, (*d2, p2.h), tol, flush, 5, out=u2)
-            row["autotuned"] = {"cell_n": bn, "ctas": bc, "ms": statistics.mean(ts) * 1e3,
+            row["autotuned"] = {"cell_n": bn, "ctas": bc,
+                                "warps_per_cell": sts[-1]["warps_per_cell_used"],
+                                "ms": statistics.mean(ts) * 1e3,
                                 "nodes_per_s": p2.nodes / statistics.mean(ts),
                                 "max_rel_err_vs_oracle": err(u2.cpu().numpy(), k2)}
         ex["osc257_" + prec] = row

@@ -105,7 +105,9 @@ typedef struct {
                                (n + 1) h / 2 over the speed at the neighbour's
                                centre, with cell values kept (not reset to
                                +inf) when a cell is taken (Sec. 7) */
-  int reserved4;            /* must be 0 */
+  int warps_per_cell;       /* warps that sweep one 16^3 cell together: 4, 6
+                               or 8 (one thread per node of the largest
+                               plane at 6); 0 = 6, or the autotuned value */
   uint64_t serve_batch_nodes; /* serving: a batch takes waiting requests until
                                  it holds this many grid nodes (at least one
                                  request); 0 = default 64 M.  Smaller batches
@@ -161,6 +163,8 @@ typedef struct {
                                    (inputs to queued exit cells), FP32 -> FP64
                                    hand-over and polish schedule, residual check +
                                    fallback + copy-out] */
+  int warps_per_cell_used;      /* warps per 16^3 cell of the min-mode sweeps */
+  int reserved_stats;
 } eik_stats;
 
 /* Default options. */
@@ -218,13 +222,16 @@ int eik_solve_device(eik_ctx *ctx, const int64_t dims[3], double h,
 
 /*
  * Autotuner.  Times the solve of a representative grid (host buffers, as
- * eik_solve) for each cell size in {4, 8, 16} (4 only up to 2^22 nodes) and
- * one or two cell-kernel CTAs per SM, keeps the fastest for this context,
- * and uses it for later solves whose size falls in the same power-of-two
- * bucket of node count while opts.cell_n and opts.max_ctas are 0.  Returns
- * the choice in *best_n / *best_ctas (either may be NULL).  Cell size 32 is
- * not offered: a 32^3 cell with its halo does not fit shared memory next to
- * its slowness.
+ * eik_solve) for each worker shape -- cells of 4^3 and 8^3 (one warp per
+ * cell; 4^3 only up to 2^22 nodes) and 16^3 cells swept by 4, 6 or 8 warps
+ * -- with one or two cell-kernel CTAs per SM, keeps the fastest for this
+ * context, and uses it for later solves whose size falls in the same
+ * power-of-two bucket of node count while opts.cell_n, opts.max_ctas and
+ * opts.warps_per_cell are 0.  Returns the cell size and CTA count in
+ * *best_n / *best_ctas (either may be NULL); the warps per cell show in
+ * eik_stats.warps_per_cell_used of later solves.  Cell size 32 is not
+ * offered: a 32^3 cell with its halo does not fit shared memory next to its
+ * slowness.
  */
 int eik_autotune(eik_ctx *ctx, const int64_t dims[3], double h, const float *F,
                  const uint8_t *src_mask, const double *q, double tol, int *best_n,

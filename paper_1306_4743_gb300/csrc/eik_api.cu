@@ -59,8 +59,11 @@ struct eik_ctx {
   int* d_off[3] = {nullptr, nullptr, nullptr};
   // serving
   ServeState* serve = nullptr;
-  // autotune results: log2(nodes) bucket -> (cell size, CTAs of the cell kernel)
-  std::map<int, std::pair<int, int>> tuned;
+  // autotune results: log2(nodes) bucket -> worker shape
+  struct Tuned {
+    int n, ctas, wpc;
+  };
+  std::map<int, Tuned> tuned;
   unsigned long long tune_generation = 0;  // bumped by every eik_autotune
 };
 
@@ -137,7 +140,7 @@ int size_bucket(long long nodes) {
 int choose_cell_n(eik_ctx* ctx, long long nodes) {
   if (ctx->opts.cell_n) return ctx->opts.cell_n;
   auto it = ctx->tuned.find(size_bucket(nodes));
-  if (it != ctx->tuned.end()) return it->second.first;
+  if (it != ctx->tuned.end()) return it->second.n;
   // built-in size table: 16^3 cells from ~128^3 nodes up (fewer, longer
   // visits keep the queue latency small against the sweeping), else 8^3
   return nodes >= (1ll << 21) ? 16 : 8;
@@ -550,10 +553,15 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.max_sweeps = ctx->opts.max_sweeps_per_visit;
   p.pass = 0;
   p.max_ctas = ctx->opts.max_ctas;
-  if (!p.max_ctas && !ctx->opts.cell_n) {
+  int wpc = ctx->opts.warps_per_cell;
+  if (!p.max_ctas && !ctx->opts.cell_n && !wpc) {
     auto it = ctx->tuned.find(size_bucket(nodes_max));
-    if (it != ctx->tuned.end()) p.max_ctas = it->second.second;
+    if (it != ctx->tuned.end()) {
+      p.max_ctas = it->second.ctas;
+      wpc = it->second.wpc;
+    }
   }
+  if (n != 16) wpc = 0;
   p.kappa_from_ctl = polish ? 1 : 0;
   p.relaxed = ctx->opts.queue_order;
   p.gated = 0;
@@ -561,7 +569,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.use_levels = 0;
   CK(cudaEventRecord(ex.ev[1], st));
   int grid_ctas = 0;
-  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas, nl));
+  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas, nl, wpc));
   CK(cudaEventRecord(ex.ev[2], st));
   if (polish) {
     const float lift = ctx->opts.polish_lift != 0.0 ? (float)ctx->opts.polish_lift : 0x1p-11f;
@@ -575,7 +583,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     p.use_levels = 1;
     CK(cudaEventRecord(ex.ev[3], st));
     // monotone FP64 sweeps down from the lifted FP32 result
-    CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr, nl));
+    CK(launch_cells(true, false, n, p, ctx->sms, st, nullptr, nl, wpc));
     CK(cudaEventRecord(ex.ev[4], st));
     // fallback, gated on the device: if some u ended below the fixed point
     // (lift too small), polish again with replace-mode sweeps
@@ -585,7 +593,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     p.pass = 2;
     p.gated = 0;
     p.use_levels = 0;
-    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr, nl));
+    CK(launch_cells(true, true, n, p, ctx->sms, st, nullptr, nl, 0));
   }
   CK(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + L.off_fin), segs, dctl,
                              polish, tol, st, nl));
@@ -603,6 +611,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   Lr.hres = hres;
   Lr.grid = grid_ctas;
   Lr.launches = nl;
+  Lr.wpc = n == 16 ? (wpc ? wpc : 6) : 1;
   return EIK_OK;
 }
 
@@ -650,6 +659,7 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
     stats->nodes = (uint64_t)nodes_total;
     stats->cell_n_used = n;
     stats->kernel_launches = (uint64_t)Lr.launches;
+    stats->warps_per_cell_used = Lr.wpc;
     stats->grid_ctas = grid_ctas;
     stats->fallback_used = hres->counters[2][kCntPushes] > 0;
     stats->fallback_visits = hres->counters[2][kCntVisits];
@@ -801,7 +811,9 @@ int eik_create(eik_ctx** out, const eik_opts* opts) {
   if (o.precision != EIK_FP64 && o.precision != EIK_FP32_POLISH) return EIK_EINVAL;
   if (o.cell_n != 0 && size_index(o.cell_n) < 0) return EIK_EINVAL;
   if (o.max_ctas < 0 || o.queue_order < 0 || o.queue_order > 1 || o.cell_key < 0 ||
-      o.cell_key > 1 || o.reserved4)
+      o.cell_key > 1 ||
+      !(o.warps_per_cell == 0 || o.warps_per_cell == 4 || o.warps_per_cell == 6 ||
+        o.warps_per_cell == 8))
     return EIK_EINVAL;
   if (o.max_sweeps_per_visit <= 0) o.max_sweeps_per_visit = 4096;
   if (!(o.bulk_kappa_rel >= 0.0) || isinf(o.bulk_kappa_rel)) return EIK_EINVAL;
@@ -883,15 +895,17 @@ int eik_autotune(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
   double* u = static_cast<double*>(malloc((size_t)nodes * sizeof(double)));
   if (!u) return EIK_ENOMEM;
   const eik_opts saved = ctx->opts;
-  const int cands_n[3] = {4, 8, 16};
+  // worker shapes: (cell size, warps per 16^3 cell)
+  const int cands[5][2] = {{4, 0}, {8, 0}, {16, 4}, {16, 6}, {16, 8}};
   double best = 1e300;
-  int bn = 0, bc = 0, rc = EIK_OK;
-  for (int ci = 0; ci < 3 && rc == EIK_OK; ++ci) {
-    const int n = cands_n[ci];
+  int bn = 0, bc = 0, bw = 0, rc = EIK_OK;
+  for (int ci = 0; ci < 5 && rc == EIK_OK; ++ci) {
+    const int n = cands[ci][0];
     if (n == 4 && nodes > (1ll << 22)) continue;  // many small cells: queue-bound
     for (int per_sm = 1; per_sm <= 2; ++per_sm) {
       ctx->opts.cell_n = n;
       ctx->opts.max_ctas = per_sm * ctx->sms;
+      ctx->opts.warps_per_cell = cands[ci][1];
       double t = 0.0;
       for (int rep = 0; rep < 2 && rc == EIK_OK; ++rep) {  // first run warms up
         eik_stats st;
@@ -902,13 +916,14 @@ int eik_autotune(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
         best = t;
         bn = n;
         bc = per_sm * ctx->sms;
+        bw = cands[ci][1];
       }
     }
   }
   ctx->opts = saved;
   free(u);
   if (rc != EIK_OK) return rc;
-  ctx->tuned[size_bucket(nodes)] = std::make_pair(bn, bc);
+  ctx->tuned[size_bucket(nodes)] = eik_ctx::Tuned{bn, bc, bw};
   ++ctx->tune_generation;  // a captured batch graph may hold the old choice
   if (best_n) *best_n = bn;
   if (best_ctas) *best_ctas = bc;

@@ -304,7 +304,7 @@ extern "C" int eik_solve_device_noalloc(const int64_t dims[3], double h, const f
   p.cell_key = 0;
   p.use_levels = 0;
   int grid = 0;
-  CKN(launch_cells(true, false, n, p, slot->sms, st, &grid, launches));
+  CKN(launch_cells(true, false, n, p, slot->sms, st, &grid, launches, 0));
   CKN(launch_residual_extract(reinterpret_cast<const FinalInstance*>(A + off_fin), segs, dctl,
                               false, 0.0, st, launches));
   CKN(cudaMemcpyAsync(&g_host_ctl, dctl, sizeof(Control), cudaMemcpyDeviceToHost, st));

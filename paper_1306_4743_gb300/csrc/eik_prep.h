@@ -100,11 +100,10 @@ cudaError_t launch_residual_extract(const FinalInstance* d_fi, const Segments& s
                                     bool after_fallback, double kappa, cudaStream_t st,
                                     int& launches);
 
-// Persistent cell kernels (eik_cells_f32.cu / eik_cells_f64.cu).
+// Persistent cell kernels (eik_cells_f32.cu / eik_cells_f64.cu /
+// eik_cells_f64r.cu).  wpc: warps per worker for 16^3 cells (4, 6 or 8;
+// 0 = 6); replace-mode kernels always use the default shape.
 cudaError_t launch_cells(bool fp64, bool replace, int n, const CellKernelParams& p, int sms,
-                         cudaStream_t st, int* grid_out, int& launches);
-
-// Shared memory bytes and threads of the cell kernel for (type, n).
-void cells_kernel_shape(bool fp64, int n, int* threads, int* smem_bytes, int* workers);
+                         cudaStream_t st, int* grid_out, int& launches, int wpc);
 
 }  // namespace eik

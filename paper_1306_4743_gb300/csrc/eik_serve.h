@@ -38,6 +38,7 @@ struct Exec {
 struct Launch {
   int count = 0, n = 0, grid = 0;
   int launches = 0;  // kernels this batch enqueued
+  int wpc = 1;       // warps per worker of the min-mode cell kernels
   bool polish = false, host_io = false, async_out = false;
   long long nodes_total = 0;
   Control* hres = nullptr;  // pinned copy of the control block

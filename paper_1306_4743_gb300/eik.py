@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("queue_order", ctypes.c_int),
                 ("bulk_kappa_rel", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("cell_key", ctypes.c_int),
-                ("reserved4", ctypes.c_int), ("serve_batch_nodes", ctypes.c_uint64),
+                ("warps_per_cell", ctypes.c_int), ("serve_batch_nodes", ctypes.c_uint64),
                 ("polish_lift", ctypes.c_double)]
 
 
@@ -74,7 +74,8 @@ class Stats(ctypes.Structure):
                 ("revisit_sweeps", ctypes.c_uint64 * 2),
                 ("revisit_updates", ctypes.c_uint64 * 2),
                 ("max_visit_sweeps", ctypes.c_uint64 * 3),
-                ("seconds_stage", ctypes.c_double * 3)]
+                ("seconds_stage", ctypes.c_double * 3),
+                ("warps_per_cell_used", ctypes.c_int), ("reserved_stats", ctypes.c_int)]
 
     def as_dict(self):
         d = {}
@@ -176,7 +177,8 @@ def default_opts() -> Opts:
 def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
               spin_cap_us=None, bucket_width=None, max_sweeps_per_visit=None, max_ctas=0,
               bulk_kappa_rel=None, queue_order=None, use_graphs=None,
-              cell_key=None, serve_batch_nodes=None, polish_lift=None) -> Opts:
+              cell_key=None, serve_batch_nodes=None, polish_lift=None,
+              warps_per_cell=None) -> Opts:
     """eik_opts from the library defaults with the given fields changed
     (None = keep the default)."""
     o = default_opts()
@@ -203,6 +205,8 @@ def make_opts(precision="fp32_polish", cell_n=0, device=0, hbm_budget_bytes=0,
         o.serve_batch_nodes = int(serve_batch_nodes)
     if polish_lift is not None:
         o.polish_lift = float(polish_lift)
+    if warps_per_cell is not None:
+        o.warps_per_cell = int(warps_per_cell)
     return o
 
 
@@ -233,7 +237,7 @@ class Solver:
                  hbm_budget_bytes=0, spin_cap_us=None, bucket_width=None,
                  max_sweeps_per_visit=None, max_ctas=0, bulk_kappa_rel=None,
                  queue_order=None, use_graphs=None, cell_key=None, serve_batch_nodes=None,
-                 polish_lift=None):
+                 polish_lift=None, warps_per_cell=None):
         """Options left at None keep the library defaults (eik_opts_default)."""
         self.lib = load()
         o = make_opts(precision=precision, cell_n=cell_n, device=device,
@@ -241,7 +245,8 @@ class Solver:
                       bucket_width=bucket_width, max_sweeps_per_visit=max_sweeps_per_visit,
                       max_ctas=max_ctas, bulk_kappa_rel=bulk_kappa_rel,
                       queue_order=queue_order, use_graphs=use_graphs, cell_key=cell_key,
-                      serve_batch_nodes=serve_batch_nodes, polish_lift=polish_lift)
+                      serve_batch_nodes=serve_batch_nodes, polish_lift=polish_lift,
+                      warps_per_cell=warps_per_cell)
         self.opts = o
         self._outputs = {}  # ticket -> output array, alive until done or cancelled
         self.ctx = ctypes.c_void_p()

@@ -74,6 +74,9 @@ def test_invalid_options_rejected_before_device_use():
     o.cell_key = 2
     assert lib.eik_create(ctypes.byref(ctx), ctypes.byref(o)) == 1
     o = eik.default_opts()
+    o.warps_per_cell = 5
+    assert lib.eik_create(ctypes.byref(ctx), ctypes.byref(o)) == 1
+    o = eik.default_opts()
     o.polish_lift = -0.75  # would start the polish far below any fixed point
     assert lib.eik_create(ctypes.byref(ctx), ctypes.byref(o)) == 1
     assert not ctx

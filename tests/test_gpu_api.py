@@ -149,6 +149,7 @@ def test_autotune_picks_and_applies(eik):
         assert n in (4, 8, 16) and ctas > 0
         u, st = s.solve(p.F, p.mask, p.q, p.h)
         assert st["cell_n_used"] == n and st["grid_ctas"] <= ctas
+        assert st["warps_per_cell_used"] in ((4, 6, 8) if n == 16 else (1,))
     assert rel_err(u, p) <= 1e-9
 
 

@@ -136,6 +136,17 @@ def test_oscillatory_129(eik, precision):
     check_against_oracle(u, p, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
+@pytest.mark.parametrize("wpc", [4, 6, 8])
+def test_worker_shapes_of_16_cubed_cells(eik, precision, wpc):
+    # 16^3 cells swept by 4, 6 or 8 warps: the same fixed point
+    p = W.oscillatory(97)
+    with eik.Solver(precision=precision, cell_n=16, warps_per_cell=wpc) as s:
+        u, st = s.solve(p.F, p.mask, p.q, p.h)
+    assert st["warps_per_cell_used"] == wpc and st["cell_n_used"] == 16
+    check_against_oracle(u, p, precision)
+
+
 def test_barrier_blocks_129(eik):
     p = W.barrier_blocks(129)
     with eik.Solver(precision="fp32_polish", cell_n=8) as s:

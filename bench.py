@@ -724,7 +724,7 @@ def run_extras(args, eik, W, torch, np, dev, local, rank, world, flush, jobs, ba
                           "ms": statistics.mean(ts) * 1e3, "cell_n": 8,
                           "max_rel_err_vs_oracle": err(u1.cpu().numpy(), ("point", 65, 500))}
     del d1, u1
-    # --- cell values of Eq. 3 against Eq. 4 (Sec. 7) on the 64^3 shell maze
+    # --- cell values of Eq. 3 against Eq. 4 (Sec. 6.8) on the 64^3 shell maze
     pm = W.shell_maze(64)
     dm = [torch.from_numpy(x).to(dev) for x in (pm.F, pm.mask, pm.q)]
     cells = (64 // 8) ** 3

@@ -63,7 +63,7 @@ typedef enum {
   EIK_FP64 = 0,        /* every sweep in double precision */
   EIK_FP32_POLISH = 1  /* bulk sweeps in single precision, then double
                           precision polishing sweeps from the single-precision
-                          result (Sec. 6.5 studies the single-precision
+                          result (Sec. 6.4 studies the single-precision
                           behaviour; the polish restores double precision) */
 } eik_precision;
 
@@ -104,7 +104,7 @@ typedef struct {
                                (default); 1 = Eq. 4, the largest one plus
                                (n + 1) h / 2 over the speed at the neighbour's
                                centre, with cell values kept (not reset to
-                               +inf) when a cell is taken (Sec. 7) */
+                               +inf) when a cell is taken (Sec. 6.8) */
   int warps_per_cell;       /* warps that sweep one 16^3 cell together: 4, 6
                                or 8 (one thread per node of the largest
                                plane at 6); 0 = 6, or the autotuned value */
@@ -193,7 +193,7 @@ int eik_struct_sizes(size_t *opts_bytes, size_t *stats_bytes);
  *   src_mask = exit set Q' (nx*ny*nz bytes), nonzero = exit node; at least one
  *   q        = exit values (nx*ny*nz doubles), read only where src_mask != 0,
  *              finite
- *   tol      = kappa of the early-termination rule of Sec. 6.4: a local
+ *   tol      = kappa of the early-termination rule of Sec. 6.3: a local
  *              update that changes a value by no more than tol does not count
  *              as a change, neither for stopping a cell's sweeps nor for
  *              flagging a neighbouring cell (tol = 0: sweep until no value

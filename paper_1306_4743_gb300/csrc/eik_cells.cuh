@@ -2,7 +2,7 @@
 // parallel Heap-Cell Method's main loop (Alg. 1 and Alg. 3).
 //
 // A worker (one warp for n <= 8, a group of WPC warps for n = 16) repeats:
-//   1. pop a cell from the lowest non-empty Dial bucket (Alg. 3 l.6-11; the
+//   1. pop a cell from the lowest non-empty Dial bucket (Alg. 3; the
 //      cell value is reset to +inf and its preferred directions are taken),
 //   2. stage the cell and its one-node face halo of u into shared memory with
 //      one TMA tensor box, and the cell's slowness with one bulk copy (the
@@ -125,7 +125,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
   using G = Geo<T, N>;
   const int i = si % N, j = (si / N) % N, k = si / (N * N);
   const T s = S[si];
-  unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
+  unsigned c1 = chg[si] & ~kActive;  // the node is no longer active (Alg. 2)
   auto activate = [&](int nb) { chg[nb] |= kActive; };
   if (vlt(s, tinf<T>())) {
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
@@ -155,7 +155,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
       }
     }
     if (big) {
-      // Alg. 2 l.8-10: neighbours (in this cell) that may now use the new
+      // Alg. 2: neighbours (in this cell) that may now use the new
       // value become active; neighbours in other cells are reached through
       // the face flags.  In min mode a neighbour y can use the new value only
       // if it is below y's own value.  (Also requiring it to be below y's
@@ -207,7 +207,7 @@ __device__ __forceinline__ bool take_node(T* __restrict__ U, const T* __restrict
                                           unsigned* __restrict__ chg, int si, T kappa,
                                           unsigned& n_updates) {
   using G = Geo<T, N>;
-  unsigned c1 = chg[si] & ~kActive;  // Alg. 2 l.4
+  unsigned c1 = chg[si] & ~kActive;  // the node is no longer active (Alg. 2)
   const T s = S[si];
   bool big = false;
   if (vlt(s, tinf<T>())) {
@@ -418,7 +418,7 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
         cur[h] = e < e1 ? ((unsigned)tab[e] ^ dmask) : kNone;
       }
     }
-    // the active bits of all of this thread's nodes first (Alg. 2 l.1-2),
+    // the active bits of all of this thread's nodes first (Alg. 2),
     // so that their loads overlap
     bool act[UNR];
 #pragma unroll
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
       cell = queue_pop_warp(cells, ctl, p.spin_cap_ns, lane, &slot, p.relaxed != 0,
                             (unsigned)(blockIdx.x * WORKERS + worker) * 7u);
       if (lane == 0 && cell >= 0) {
-        // V^c <- +inf (Alg. 1 l.5); the Eq. 4 variant keeps it (Sec. 7)
+        // V^c <- +inf (Alg. 1); the Eq. 4 variant keeps it (Sec. 6.8)
         if (p.cell_key == 0) atomicExch(cells.key + cell, kKeyInf);
         pref = atomicAnd(cells.dir + cell, kDirVisited);  // take dirs and faces
       }

@@ -688,8 +688,8 @@ static __device__ int queue_pop_warp(const CellArrays& c, Control* ctl,
   }
 }
 
-// Tell cell `nb` that a neighbour changed its inflow border (Alg. 2 lines 8-14
-// and Alg. 3 lines 20-28): lower its cell value (Eq. 3), add preferred
+// Tell cell `nb` that a neighbour changed its inflow border (the neighbour
+// flagging steps of Alg. 2 and Alg. 3): lower its cell value (Eq. 3), add preferred
 // directions, and queue it unless it is queued or dirty already.  A running
 // cell is marked DIRTY and re-queues itself when its visit ends.  The
 // caller has made its new border values visible (__threadfence) before.

@@ -68,7 +68,7 @@ struct Instance {
   int ncx, ncy, ncz;     // cells per axis
   int cell_base;         // global id of the first cell
   int ncells;
-  double kappa;          // change threshold of Sec. 6.4
+  double kappa;          // change threshold of Sec. 6.3 (early sweep terminations)
 };
 
 // Queue and solver control words, one block in device memory.  The words

@@ -1,5 +1,5 @@
 // eik_prep.cu -- streaming kernels around the persistent cell kernel:
-// grid initialisation (Alg. 3 l.1-4 with the LSM initialisation of Sec. 4),
+// grid initialisation (the set-up steps of Alg. 3, with the LSM initialisation of Sec. 4),
 // cell-value initialisation, queue seeding, the FP32 -> FP64 hand-over of
 // the polish, the FP64 residual check and the copy-out to the caller layout.
 #include "eik_device.cuh"
@@ -299,7 +299,7 @@ __global__ void setup_bulk_kernel(Control* ctl, const int* n_src, int count, int
   ctl->queued = 0;
 }
 
-// Queue every cell that holds an exit node (Alg. 1 l.2).
+// Queue every cell that holds an exit node (the first step of Alg. 1).
 __global__ void seed_sources_kernel(int total_cells, CellArrays c, Control* ctl, int pass) {
   if (ctl->status) return;
   unsigned long long pushes = 0;

@@ -205,7 +205,7 @@ def test_paper_workloads(eik, precision, name):
 @pytest.mark.parametrize("precision", ["fp64", "fp32_polish"])
 @pytest.mark.parametrize("name", ["maze_64", "ex2_96", "checker11_88"])
 def test_eq4_cell_values(eik, precision, name):
-    # The older cell-value heuristic of Sec. 7 (Eq. 4, no reset on pop)
+    # The older cell-value heuristic of Sec. 6.8 (Eq. 4, no reset on pop)
     # changes the schedule only: the result is the same fixed point.
     p = PAPER_WORKLOADS[name]()
     with eik.Solver(precision=precision, cell_key=1) as s:

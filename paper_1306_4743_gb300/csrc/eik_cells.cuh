@@ -43,7 +43,16 @@ __device__ __forceinline__ bool vlt(double a, double b) { return dlt_nn(a, b); }
 // 32-bit word per node: sub-word shared-memory accesses cost about twice
 // the latency of word accesses, and these bits sit on the sweep's
 // critical path.
-constexpr unsigned kWritten = 1, kBig = 2, kActive = 4;
+// The active bit sits alone in byte 0 and the others in byte 1, so that a
+// neighbour is activated by a single byte store, without reading the word
+// (two threads of one plane step may activate the same neighbour; they store
+// the same byte, and the neighbour's own bits are written only by the thread
+// that updates it, on another plane step).
+constexpr unsigned kActive = 0x4u, kWritten = 0x100u, kBig = 0x200u;
+
+__device__ __forceinline__ void activate_node(unsigned* chg, int nb) {
+  reinterpret_cast<unsigned char*>(chg + nb)[0] = (unsigned char)kActive;
+}
 
 template <typename T, int N>
 struct Geo {
@@ -126,7 +135,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
   const int i = si % N, j = (si / N) % N, k = si / (N * N);
   const T s = S[si];
   unsigned c1 = chg[si] & ~kActive;  // the node is no longer active (Alg. 2)
-  auto activate = [&](int nb) { chg[nb] |= kActive; };
+  auto activate = [&](int nb) { activate_node(chg, nb); };
   if (vlt(s, tinf<T>())) {
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
     const T v = U[t];
@@ -145,13 +154,13 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
       }
       if (lower) {
         U[t] = nv;
-        c1 |= big ? 3 : 1;
+        c1 |= big ? (kWritten | kBig) : kWritten;
       }
     } else {
       big = nv != v && fabs(nv - v) > kappa + fabs(v) * (T)8.8817841970012523e-16;
       if (nv != v) {
         U[t] = nv;
-        c1 |= big ? 3 : 1;
+        c1 |= big ? (kWritten | kBig) : kWritten;
       }
     }
     if (big) {
@@ -198,10 +207,9 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
 // recompute it from its six neighbours (Eq. 2), store a lower value, and
 // return whether it changed by more than kappa.  wake_users: activate the
 // neighbours of si that may now use its value (below the neighbour and
-// below the neighbour's other neighbour on that axis); a neighbour that is
-// still active is left alone.  In the wake step no thread writes a flag
-// word except to set kActive, so concurrent activations of one neighbour
-// all store the same word and need no atomics.
+// below the neighbour's other neighbour on that axis).  In the wake step no
+// thread writes a flag word except the active byte, so concurrent
+// activations of one neighbour all store the same byte and need no atomics.
 template <typename T, int N>
 __device__ __forceinline__ bool take_node(T* __restrict__ U, const T* __restrict__ S,
                                           unsigned* __restrict__ chg, int si, T kappa,
@@ -236,8 +244,7 @@ __device__ __forceinline__ void wake_users(const T* __restrict__ U, unsigned* __
   const T nv = U[t];
   auto consider = [&](bool inside, int ny, int ty, int tf) {
     if (inside) {
-      const unsigned w = chg[ny];
-      if (!(w & kActive) && vlt(nv, U[ty]) && vlt(nv, U[tf])) chg[ny] = w | kActive;
+      if (vlt(nv, U[ty]) && vlt(nv, U[tf])) activate_node(chg, ny);
     }
   };
   consider(i > 0, si - 1, t - 1, t - 2);
@@ -767,7 +774,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
           if (axis == 0) { i = upper ? N - 1 : 0; j = a; k = b; }
           else if (axis == 1) { i = a; j = upper ? N - 1 : 0; k = b; }
           else { i = a; j = b; k = upper ? N - 1 : 0; }
-          if (chg[i + N * (j + N * k)] & 2u) {
+          if (chg[i + N * (j + N * k)] & kBig) {
             const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
             const int step = axis == 0 ? 1 : axis == 1 ? G::SY : G::SZ;
             const T vi = U[t];
@@ -808,7 +815,7 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     }
     worker_sync<WPC>(worker);
     for (int e = tid; e < G::N3; e += NT) {
-      if (chg[e] & 1u) {
+      if (chg[e] & kWritten) {
         const int i = e % N, j = (e / N) % N, k = e / (N * N);
         gu[g0 + i + px * j + pxy * k] = U[(i + 1) + G::SY * (j + 1) + G::SZ * (k + 1)];
       }

@@ -681,6 +681,7 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi,
   const BlockWork w = block_work(seg, count, kRowsPerBlock);
   const FinalInstance P = fi[w.inst];
   const double qb = q_base(ctl);
+  const bool shift = qb != 0.0;
   const double* u = static_cast<const double*>(P.u64);
   const double* s = static_cast<const double*>(P.s64);
   const int lg = __ffs(P.n) - 1, nm = P.n - 1;
@@ -700,15 +701,18 @@ __global__ void residual_extract_kernel(const FinalInstance* __restrict__ fi,
       const long long t = tbase + i;
       const double v = u[t];
       const long long e = rbase + i;
-      P.out[e] = P.mask[e] ? P.q[e] : (qb == 0.0 ? v : v + qb);
-      if (!isfinite(v)) {
+      P.out[e] = P.mask[e] ? P.q[e] : (shift ? v + qb : v);
+      // finiteness and the exit test on the bit patterns (stored values and
+      // s are >= 0): each FP64 compare costs a slot of the narrow FP64 pipe,
+      // which this pass is bound by
+      if ((__double_as_longlong(v) & 0x7ff0000000000000ll) == 0x7ff0000000000000ll) {
         ++nbad;
         continue;
       }
       const unsigned long long o = ord_of_double(v);
       umax = o > umax ? o : umax;
       const double sv = s[(cbase + (i >> lg)) * N3 + (i & nm) + in_cell];
-      if (!(sv < CUDART_INF)) continue;  // exit node
+      if (dbits(sv) >= dbits(CUDART_INF)) continue;  // exit node
       const double ax = nmin(u[t - 1], u[t + 1]);
       const double ay = nmin(u[t - sy], u[t + sy]);
       const double az = nmin(u[t - sz], u[t + sz]);

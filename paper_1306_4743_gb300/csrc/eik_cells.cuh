@@ -567,9 +567,12 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
 
     // ---- 2. stage cell + halo ------------------------------------------
     // (and, for the level pass of the polish, the cell's level table)
+    // The level pass serves first visits: a revisit starts from a few
+    // flagged face nodes, and walking all levels for them (two barriers a
+    // level) cost more than sweeping from those faces.
     int lev_depth = 0;
     if constexpr (!REPLACE && sizeof(T) == 8)
-      if (p.use_levels) lev_depth = cells.lev_depth[cell];
+      if (p.use_levels && !(pref & kDirVisited)) lev_depth = cells.lev_depth[cell];
     fence_proxy_async_smem();
     worker_sync<WPC>(worker);
     if (tid == 0) {

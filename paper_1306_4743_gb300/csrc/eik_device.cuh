@@ -53,6 +53,27 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+// 64-bit compare-and-swap with release (acquire) ordering at GPU scope.
+__device__ __forceinline__ unsigned long long cas_release_u64(unsigned long long* p,
+                                                              unsigned long long cmp,
+                                                              unsigned long long val) {
+  unsigned long long old;
+  asm volatile("atom.release.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(old)
+               : "l"(p), "l"(cmp), "l"(val)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long cas_acquire_u64(unsigned long long* p,
+                                                              unsigned long long cmp,
+                                                              unsigned long long val) {
+  unsigned long long old;
+  asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(old)
+               : "l"(p), "l"(cmp), "l"(val)
+               : "memory");
+  return old;
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -433,9 +454,9 @@ __device__ __forceinline__ void stack_push(unsigned long long* head, const CellA
   unsigned long long old = ld_relaxed_u64(head);
   for (;;) {
     c.next[cell] = (unsigned)(old & 0xffffffffull);
-    __threadfence();
+    // release: the link above is visible before the new head
     const unsigned long long nw = (((old >> 32) + 1ull) << 32) | (unsigned long long)(cell + 1u);
-    const unsigned long long prev = atomicCAS(head, old, nw);
+    const unsigned long long prev = cas_release_u64(head, old, nw);
     if (prev == old) return;
     old = prev;
   }
@@ -451,11 +472,9 @@ __device__ __forceinline__ int stack_pop(unsigned long long* head, const CellArr
     const unsigned cell = top - 1u;
     const unsigned nxt = ld_relaxed_u32(c.next + cell);
     const unsigned long long nw = (((old >> 32) + 1ull) << 32) | (unsigned long long)nxt;
-    const unsigned long long prev = atomicCAS(head, old, nw);
-    if (prev == old) {
-      __threadfence();
-      return (int)cell;
-    }
+    // acquire: what the pusher wrote before its release is visible after
+    const unsigned long long prev = cas_acquire_u64(head, old, nw);
+    if (prev == old) return (int)cell;
     old = prev;
   }
 }

@@ -117,3 +117,36 @@ def test_cancel_waiting_and_running(eik):
         assert all(v[0] == 0 for v in done.values())
         ok, rc, _ = s.poll(tickets[0])
         assert not ok and rc == 9
+
+
+def test_sharded_server_over_real_solvers(eik):
+    """dispatch.ShardedServer with two library contexts as its backends (both
+    on cuda:0 here; on a multi-GPU node each would be one device): requests
+    are spread by outstanding nodes, every result matches the oracle, and the
+    per-backend counts add up."""
+    from paper_1306_4743_gb300 import dispatch
+    probs = _requests()
+    backs = [eik.Solver(precision="fp32_polish", device=0),
+             eik.Solver(precision="fp64", device=0)]
+    srv = dispatch.ShardedServer(backs, budgets=[8 << 30, 8 << 30])
+    tickets = {}
+    for k, p in enumerate(probs):
+        t, u = srv.submit(p.F, p.mask, p.q, p.h)
+        tickets[t] = (k, u)
+    seen = []
+    t0 = time.time()
+    while tickets:
+        for t in list(tickets):
+            ok, rc, st = srv.poll(t)
+            if ok:
+                k, u = tickets.pop(t)
+                assert rc == 0, (k, rc)
+                p = probs[k]
+                ref = oracle.fmm(p.F, p.mask, p.q, p.h)
+                bound = TOL if st["backend"] == 0 else 1e-10
+                assert np.max(np.abs(u - ref)) <= bound * np.max(ref), k
+                seen.append(st["backend"])
+        assert time.time() - t0 < 120, "sharded serving did not finish"
+    srv.close()
+    assert sorted(set(seen)) == [0, 1] and len(seen) == len(probs)
+    assert srv.outstanding == [0, 0]

@@ -106,8 +106,10 @@ typedef struct {
                                centre, with cell values kept (not reset to
                                +inf) when a cell is taken (Sec. 6.8) */
   int warps_per_cell;       /* warps that sweep one 16^3 cell together: 4, 6
-                               or 8 (one thread per node of the largest
-                               plane at 6); 0 = 6, or the autotuned value */
+                               or 8 (6: one thread per node of the largest
+                               plane; 8: one thread per (j, k) pencil); 0 =
+                               the autotuned value, else 8 for the FP32 bulk
+                               and 6 for FP64 sweeps */
   uint64_t serve_batch_nodes; /* serving: a batch takes waiting requests until
                                  it holds this many grid nodes (at least one
                                  request); 0 = default 64 M.  Smaller batches
@@ -163,7 +165,7 @@ typedef struct {
                                    (inputs to queued exit cells), FP32 -> FP64
                                    hand-over and polish schedule, residual check +
                                    fallback + copy-out] */
-  int warps_per_cell_used;      /* warps per 16^3 cell of the min-mode sweeps */
+  int warps_per_cell_used;      /* warps per 16^3 cell of the bulk sweeps */
   int reserved_stats;
 } eik_stats;
 
@@ -223,8 +225,9 @@ int eik_solve_device(eik_ctx *ctx, const int64_t dims[3], double h,
 /*
  * Autotuner.  Times the solve of a representative grid (host buffers, as
  * eik_solve) for each worker shape -- cells of 4^3 and 8^3 (one warp per
- * cell; 4^3 only up to 2^22 nodes) and 16^3 cells swept by 4, 6 or 8 warps
- * -- with one or two cell-kernel CTAs per SM, keeps the fastest for this
+ * cell; 4^3 only up to 2^22 nodes) and 16^3 cells with the default shapes
+ * (8 warps for the FP32 bulk, 6 for FP64 sweeps) or 4, 6 or 8 warps in every
+ * pass -- with one or two cell-kernel CTAs per SM, keeps the fastest for this
  * context, and uses it for later solves whose size falls in the same
  * power-of-two bucket of node count while opts.cell_n, opts.max_ctas and
  * opts.warps_per_cell are 0.  Returns the cell size and CTA count in

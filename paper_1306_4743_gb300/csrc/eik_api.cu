@@ -562,6 +562,10 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
     }
   }
   if (n != 16) wpc = 0;
+  // default shapes per pass: the FP32 bulk sweeps 16^3 cells with 8 warps
+  // (one thread per (j, k) pencil, planes computed instead of read from the
+  // table: measured ~5% faster than 6 warps), FP64 sweeps with 6 warps
+  const int wpc_bulk = wpc ? wpc : (n == 16 && polish ? 8 : 0);
   p.kappa_from_ctl = polish ? 1 : 0;
   p.relaxed = ctx->opts.queue_order;
   p.gated = 0;
@@ -569,7 +573,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   p.use_levels = 0;
   CK(cudaEventRecord(ex.ev[1], st));
   int grid_ctas = 0;
-  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas, nl, wpc));
+  CK(launch_cells(!polish, false, n, p, ctx->sms, st, &grid_ctas, nl, wpc_bulk));
   CK(cudaEventRecord(ex.ev[2], st));
   if (polish) {
     const float lift = ctx->opts.polish_lift != 0.0 ? (float)ctx->opts.polish_lift : 0x1p-11f;
@@ -611,7 +615,7 @@ int eik_launch_batch(eik_ctx* ctx, Exec& ex, int count, const int64_t* dims, con
   Lr.hres = hres;
   Lr.grid = grid_ctas;
   Lr.launches = nl;
-  Lr.wpc = n == 16 ? (wpc ? wpc : 6) : 1;
+  Lr.wpc = n == 16 ? (wpc_bulk ? wpc_bulk : 6) : 1;
   return EIK_OK;
 }
 
@@ -895,11 +899,12 @@ int eik_autotune(eik_ctx* ctx, const int64_t dims[3], double h, const float* F,
   double* u = static_cast<double*>(malloc((size_t)nodes * sizeof(double)));
   if (!u) return EIK_ENOMEM;
   const eik_opts saved = ctx->opts;
-  // worker shapes: (cell size, warps per 16^3 cell)
-  const int cands[5][2] = {{4, 0}, {8, 0}, {16, 4}, {16, 6}, {16, 8}};
+  // worker shapes: (cell size, warps per 16^3 cell; 0 = the default shape of
+  // each pass)
+  const int cands[6][2] = {{4, 0}, {8, 0}, {16, 0}, {16, 4}, {16, 6}, {16, 8}};
   double best = 1e300;
   int bn = 0, bc = 0, bw = 0, rc = EIK_OK;
-  for (int ci = 0; ci < 5 && rc == EIK_OK; ++ci) {
+  for (int ci = 0; ci < 6 && rc == EIK_OK; ++ci) {
     const int n = cands[ci][0];
     if (n == 4 && nodes > (1ll << 22)) continue;  // many small cells: queue-bound
     for (int per_sm = 1; per_sm <= 2; ++per_sm) {

@@ -415,9 +415,20 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
   // faster than loading them two planes ahead: a barrier waits for loads
   // still in flight.
   unsigned left = 0;
+  // FP32 with one thread per (j, k) pencil of a 16^3 cell (8 warps): a
+  // thread's node on plane C is (C - j - k, j, k) in the sweep's reflected
+  // coordinates, computed instead of read from the plane table (one
+  // dependent shared load less per plane step; measured ~5% faster bulk
+  // sweeps than 6 warps with the table.  FP64 stays with the packed table:
+  // its narrow pipe is paid per warp instruction, and small planes then keep
+  // fewer warps busy)
+  constexpr bool PENCILS = sizeof(T) == 4 && N == 16 && NT == 256;
   for (int C = first; C < G::NPLANES; ++C) {
     unsigned cur[UNR];
-    {
+    if constexpr (PENCILS) {
+      const int jr = tid & 15, kr = tid >> 4, ir = C - jr - kr;
+      cur[0] = (ir >= 0 && ir < 16) ? ((unsigned)(ir + 16 * jr + 256 * kr) ^ dmask) : kNone;
+    } else {
       const int b0 = off[C], e1 = off[C + 1];
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {

@@ -153,6 +153,17 @@ def test_autotune_picks_and_applies(eik):
     assert rel_err(u, p) <= 1e-9
 
 
+def test_default_worker_shapes(eik):
+    # 16^3 cells: the FP32 bulk sweeps with 8 warps (one per (j, k) pencil),
+    # FP64 sweeps with 6
+    p = W.oscillatory(97)
+    for precision, wpc in (("fp32_polish", 8), ("fp64", 6)):
+        with eik.Solver(precision=precision, cell_n=16) as s:
+            u, st = s.solve(p.F, p.mask, p.q, p.h)
+        assert st["warps_per_cell_used"] == wpc, precision
+        assert rel_err(u, p) <= (1e-9 if precision == "fp32_polish" else 1e-10)
+
+
 def test_batch_graph_replay_reads_current_inputs(eik, torch):
     dev = torch.device("cuda", 0)
     probs = [W.gaussian_bumps(d, 300 + k) for k, d in enumerate([(33, 33, 65), (41, 29, 23)])]

@@ -116,7 +116,8 @@ def bytes_per_visit(n, es_u):
 # The sources that define the cell kernel: a traffic figure recorded in
 # profiles/ holds only while these are unchanged.
 CELL_KERNEL_SOURCES = ("eik_cells.cuh", "eik_cells_launch.cuh", "eik_cells_f32.cu",
-                       "eik_cells_f64.cu", "eik_device.cuh", "eik_internal.h")
+                       "eik_cells_f64.cu", "eik_device.cuh", "eik_internal.h",
+                       "eik_prep.cu", "eik_api.cu")
 
 
 def kernel_source_hash():
@@ -564,6 +565,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": workload_desc(args), "nodes": p.nodes,
                    "cell_n": n, "precision": args.precision, "tol": args.tol,
+                   "bulk_kappa": last["bulk_kappa"],
                    "error_bound": "max|u - u_FMM| <= %.0e max(u)" % BOUND[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MB L2 flush between steps (outside the step events); the "

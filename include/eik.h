@@ -91,11 +91,16 @@ typedef struct {
                                (default) */
   double bulk_kappa_rel;    /* EIK_FP32_POLISH only: change threshold of the
                                FP32 bulk sweeps, in units of (cell edge x front
-                               slowness) (default 1e-2).  Stopping the bulk
-                               early leaves values high, never low, and the
-                               FP64 polish starts above the fixed point, so
-                               this trades bulk sweeps for polish sweeps and
-                               does not change the result. */
+                               slowness).  Stopping the bulk early leaves
+                               values high, never low, and the FP64 polish
+                               starts above the fixed point, so this trades
+                               bulk sweeps for polish sweeps and does not
+                               change the result.  0 (default) = chosen per
+                               solve from the dispersion of s = h / F over the
+                               launch, r = mean(s) mean(1 / s): 3e-3 r^2, at
+                               most 1 (fine where s is nearly uniform, coarse
+                               where it spreads widely and fronts revisit
+                               cells along faster detours). */
   int use_graphs;           /* eik_solve_batch_device: capture the launch
                                sequence as a CUDA graph and replay it while
                                the arguments repeat (default 1) */
@@ -167,6 +172,8 @@ typedef struct {
                                    fallback + copy-out] */
   int warps_per_cell_used;      /* warps per 16^3 cell of the bulk sweeps */
   int reserved_stats;
+  double bulk_kappa;            /* EIK_FP32_POLISH: the change threshold the
+                                   bulk sweeps used (absolute); 0 for EIK_FP64 */
 } eik_stats;
 
 /* Default options. */

@@ -680,6 +680,7 @@ int eik_finish_batch(eik_ctx* ctx, Exec& ex, Launch& Lr, eik_stats* stats) {
     }
     for (int ps = 0; ps < 3; ++ps) stats->max_visit_sweeps[ps] = hres->counters[ps][kCntMaxSweeps];
     stats->precision_used = polish ? EIK_FP32_POLISH : EIK_FP64;
+    stats->bulk_kappa = polish ? hres->kappa_bulk : 0.0;
     double r;
     unsigned long long rb = hres->resid_bits;
     memcpy(&r, &rb, 8);
@@ -775,7 +776,7 @@ int eik_opts_default(eik_opts* o) {
   o->spin_cap_us = 5000000ull;
   o->bucket_width = 0.25;
   o->max_sweeps_per_visit = 4096;
-  o->bulk_kappa_rel = 1.0e-2;
+  o->bulk_kappa_rel = 0.0;  // chosen from the field
   o->queue_order = 1;
   o->use_graphs = 1;
   return EIK_OK;

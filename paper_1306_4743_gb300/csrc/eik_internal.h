@@ -86,6 +86,7 @@ struct Control {
   int n_sources;              // exit nodes seen by the init kernel
   int bad_input;              // an input failed validation
   double sum_inv_s;           // sum of 1 / s = F / h over non-exit nodes
+  double sum_s;               // sum of s = h / F over the same nodes
   unsigned long long n_s;     // number of terms in sum_inv_s
   unsigned long long min_q_ord;    // ordered bits of min q (double)
   unsigned long long umax_bits;    // ordered bits of the largest finite u

@@ -75,7 +75,8 @@ class Stats(ctypes.Structure):
                 ("revisit_updates", ctypes.c_uint64 * 2),
                 ("max_visit_sweeps", ctypes.c_uint64 * 3),
                 ("seconds_stage", ctypes.c_double * 3),
-                ("warps_per_cell_used", ctypes.c_int), ("reserved_stats", ctypes.c_int)]
+                ("warps_per_cell_used", ctypes.c_int), ("reserved_stats", ctypes.c_int),
+                ("bulk_kappa", ctypes.c_double)]
 
     def as_dict(self):
         d = {}

@@ -202,22 +202,22 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
   chg[si] = c1;
 }
 
-// Level-pass helpers (min mode, Alg. 2).  take_node: node si is active and
-// no other thread writes its flag word in this step: clear its active bit,
-// recompute it from its six neighbours (Eq. 2), store a lower value, and
-// return whether it changed by more than kappa.  wake_users: activate the
-// neighbours of si that may now use its value (below the neighbour and
-// below the neighbour's other neighbour on that axis).  In the wake step no
-// thread writes a flag word except the active byte, so concurrent
-// activations of one neighbour all store the same byte and need no atomics.
+// Level-pass helpers (min mode, Alg. 2).  During the level pass bits 16-31
+// of a node's flag word hold the step in which the pass took it (kNotTaken
+// before, and for fixed nodes, which are in no level).  take_node: no other
+// thread writes node si's flag word in this step: record the step, clear the
+// active bit, recompute the node from its six neighbours (Eq. 2), store a
+// lower value and mark a change by more than kappa (kBig).
+constexpr int kStepShift = 16;
+constexpr unsigned kNotTaken = 0xffffu;
+
 template <typename T, int N>
-__device__ __forceinline__ bool take_node(T* __restrict__ U, const T* __restrict__ S,
+__device__ __forceinline__ void take_node(T* __restrict__ U, const T* __restrict__ S,
                                           unsigned* __restrict__ chg, int si, T kappa,
-                                          unsigned& n_updates) {
+                                          unsigned step, unsigned& n_updates) {
   using G = Geo<T, N>;
-  unsigned c1 = chg[si] & ~kActive;  // the node is no longer active (Alg. 2)
+  unsigned c1 = (chg[si] & ~kActive & 0xffffu) | (step << kStepShift);
   const T s = S[si];
-  bool big = false;
   if (vlt(s, tinf<T>())) {
     const int i = si % N, j = (si / N) % N, k = si / (N * N);
     const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
@@ -227,45 +227,63 @@ __device__ __forceinline__ bool take_node(T* __restrict__ U, const T* __restrict
     ++n_updates;
     if (vlt(nv, v)) {
       U[t] = nv;
-      big = drop_exceeds(nv, v, (float)kappa);
-      c1 |= big ? (kWritten | kBig) : kWritten;
+      c1 |= drop_exceeds(nv, v, (float)kappa) ? (kWritten | kBig) : kWritten;
     }
   }
   chg[si] = c1;
-  return big;
 }
 
-template <typename T, int N>
-__device__ __forceinline__ void wake_users(const T* __restrict__ U, unsigned* __restrict__ chg,
-                                           int si) {
+// After the level pass, in parallel over the cell: a node x taken in step
+// sx read the values its neighbours had then.  A neighbour y taken in the
+// same or a later step, with a change above kappa, that x may now use (y
+// below x and below x's other neighbour on that axis) leaves x active for
+// the sweeps.  (The same test as waking y's users right after y's step, done
+// once for all nodes: the final values of x and of x's other neighbour are
+// the ones x kept since its step or that the wake would have compared
+// with, so no step of the pass waits for it.)  Each thread writes only its
+// own nodes' active bytes; the bits it reads of other words do not change.
+template <typename T, int N, int WPC>
+__device__ __forceinline__ void level_check(const T* __restrict__ U, unsigned* __restrict__ chg,
+                                            int tid) {
   using G = Geo<T, N>;
-  const int i = si % N, j = (si / N) % N, k = si / (N * N);
-  const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
-  const T nv = U[t];
-  auto consider = [&](bool inside, int ny, int ty, int tf) {
-    if (inside) {
-      if (vlt(nv, U[ty]) && vlt(nv, U[tf])) activate_node(chg, ny);
+  constexpr int NT = WPC * 32;
+  for (int e = tid; e < G::N3; e += NT) {
+    const unsigned sx = chg[e] >> kStepShift;
+    if (sx == kNotTaken) continue;
+    const int i = e % N, j = (e / N) % N, k = e / (N * N);
+    const bool in[6] = {i > 0, i < N - 1, j > 0, j < N - 1, k > 0, k < N - 1};
+    const int dn[3] = {1, N, N * N};
+    unsigned later = 0;  // bit d: the neighbour on side d changed in a step >= sx
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (!in[d]) continue;
+      const unsigned cy = chg[e + ((d & 1) ? dn[d >> 1] : -dn[d >> 1])];
+      if ((cy & kBig) && (cy >> kStepShift) >= sx) later |= 1u << d;
     }
-  };
-  consider(i > 0, si - 1, t - 1, t - 2);
-  consider(i < N - 1, si + 1, t + 1, t + 2);
-  consider(j > 0, si - N, t - G::SY, t - 2 * G::SY);
-  consider(j < N - 1, si + N, t + G::SY, t + 2 * G::SY);
-  consider(k > 0, si - N * N, t - G::SZ, t - 2 * G::SZ);
-  consider(k < N - 1, si + N * N, t + G::SZ, t + 2 * G::SZ);
+    if (!later) continue;
+    const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
+    const int dt[3] = {1, G::SY, G::SZ};
+    const T v = U[t];
+    bool act = false;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (!((later >> d) & 1u)) continue;
+      const int o = (d & 1) ? dt[d >> 1] : -dt[d >> 1];
+      const T uy = U[t + o];
+      act = act || (vlt(uy, v) && vlt(uy, U[t - o]));
+    }
+    if (act) activate_node(chg, e);
+  }
 }
 
 // One pass over a cell's nodes in the level order of its table (see
-// polish_levels_kernel): level by level, the active nodes of a level
-// together.  A node's FP32 upwind neighbours have smaller levels, so where
-// the FP64 values keep the FP32 order one pass settles the cell; a node
-// whose FP64 inflow comes from a later node is left active.  Each chunk of a
-// level (UNR nodes a thread) runs in two steps split by a barrier: every
-// node first takes its new value, and only then are the neighbours that can
-// use a new value woken, comparing with their settled values (without the
-// split a node would compare with a same-level neighbour still at its
-// lifted start value and wake it for nothing).  perm and loff are the
-// staged table (node indices, level starts).
+// polish_levels_kernel; fixed nodes are in no level): level by level, every
+// node of a level is taken (a first visit starts with no node active), in
+// steps of UNR nodes a thread split by a barrier.  A node's FP32 upwind
+// neighbours have smaller levels, so where the FP64 values keep the FP32
+// order one pass settles the cell; level_check then leaves active the nodes
+// whose FP64 inflow came from a node taken in the same or a later step.
+// perm and loff are the staged table (node indices, level starts).
 template <typename T, int N, int WPC>
 __device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restrict__ S,
                                            unsigned* __restrict__ chg,
@@ -274,25 +292,20 @@ __device__ __forceinline__ void level_pass(T* __restrict__ U, const T* __restric
                                            int tid, int worker, T kappa, unsigned& n_updates) {
   constexpr int NT = WPC * 32;
   constexpr int UNR = 2;
+  unsigned step = 0;
   for (int l = 0; l < depth; ++l) {
     const int lo = loff[l], hi = loff[l + 1];
-    for (int c0 = lo; c0 < hi; c0 += UNR * NT) {
-      int mine[UNR];  // node taken with a change above kappa, else -1
+    for (int c0 = lo; c0 < hi; c0 += UNR * NT, ++step) {
 #pragma unroll
       for (int h = 0; h < UNR; ++h) {
         const int e = c0 + tid + h * NT;
-        const int si = e < hi ? (int)perm[e] : -1;
-        mine[h] = -1;
-        if (si >= 0 && (chg[si] & kActive) && take_node<T, N>(U, S, chg, si, kappa, n_updates))
-          mine[h] = si;
+        if (e < hi) take_node<T, N>(U, S, chg, (int)perm[e], kappa, step, n_updates);
       }
-      worker_sync<WPC>(worker);
-#pragma unroll
-      for (int h = 0; h < UNR; ++h)
-        if (mine[h] >= 0) wake_users<T, N>(U, chg, mine[h]);
       worker_sync<WPC>(worker);
     }
   }
+  level_check<T, N, WPC>(U, chg, tid);
+  worker_sync<WPC>(worker);
 }
 
 // Worker-wide sums of the three packed per-axis counts of left-behind
@@ -599,13 +612,15 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
                   (unsigned)((kMaxLevels + 1) * 2), bar);
       }
     }
-    // On a first visit every node starts active.  After a converged visit
+    // On a first visit every node starts active, except with a level table,
+    // whose pass takes every non-fixed node anyway.  After a converged visit
     // only the halo can have changed (a cell's nodes have one writer, the
     // cell), so only the nodes on the faces flagged since then start active.
     const bool revisit = (pref & kDirVisited) != 0;
     const unsigned faces = (pref >> kFaceShift) & 0x3fu;
     {
-      const unsigned fill = revisit ? 0u : (unsigned)kActive;
+      const unsigned fill =
+          revisit ? 0u : (lev_depth > 0 ? (kNotTaken << kStepShift) : (unsigned)kActive);
       for (int e = tid * 4; e < G::N3; e += NT * 4)
         *reinterpret_cast<uint4*>(chg + e) = make_uint4(fill, fill, fill, fill);
     }

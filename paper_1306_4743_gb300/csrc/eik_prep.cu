@@ -533,11 +533,14 @@ __global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi,
 // no in-cell upwind neighbour, and a node joins the layer after the one in
 // which its last upwind neighbour was taken (so level = longest upwind
 // chain).  Each layer is appended to the node list in shared memory and
-// becomes a run of lev_perm; lev_off[l] is where layer l starts.  One block
-// per cell; cells deeper than kMaxLevels - 1 get no table (lev_depth 0).
+// becomes a run of lev_perm; lev_off[l] is where layer l starts.  Fixed
+// nodes (exits and the filler of partial cells, s = +inf) are in no layer
+// and are no node's upwind neighbour: their values never change, so
+// lev_off[depth] is the number of nodes the pass computes.  One block per
+// cell; cells deeper than kMaxLevels - 1 get no table (lev_depth 0).
 __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int total_cells,
                                      CellArrays c) {
-  __shared__ unsigned char up[4096];   // bit 2a: -axis a neighbour upwind, 2a + 1: +axis a
+  __shared__ unsigned char up[4096];   // bit 2a: -axis a neighbour upwind, 2a + 1: +axis a; bit 7: fixed
   __shared__ unsigned indeg[1024];     // upwind neighbours not yet taken, a byte per node
   __shared__ unsigned short lst[4096];  // nodes in level order
   __shared__ unsigned short offs[kMaxLevels + 1];
@@ -553,25 +556,33 @@ __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int 
     if (threadIdx.x == 0) tail = 0;
     for (int w = threadIdx.x; w < (N3 + 3) / 4; w += blockDim.x) indeg[w] = 0u;
     __syncthreads();
+    // bit 7 of up[]: the node is fixed
+    const double* sc = s64 + (long long)lc * N3;
+    for (int r = threadIdx.x; r < N3; r += blockDim.x)
+      up[r] = sc[r] < CUDART_INF ? (unsigned char)0 : (unsigned char)0x80;
+    __syncthreads();
     for (int r = threadIdx.x; r < N3; r += blockDim.x) {
       const int a = r & nm, b = (r >> lg) & nm, cc = r >> (2 * lg);
       unsigned m = 0;
-      if (s64[(long long)lc * N3 + r] < CUDART_INF) {
+      const bool fixed = (up[r] & 0x80) != 0;
+      if (!fixed) {
         const long long t = (long long)(N * cx + a + 1) + sy * (N * cy + b + 1) + sz * (N * cz + cc + 1);
         const float v = u32[t];
         const int co[3] = {a, b, cc};
         const long long st[3] = {1, sy, sz};
+        const int sl[3] = {1, N, N * N};
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
           const float lo = u32[t - st[ax]], hi = u32[t + st[ax]];
-          if (co[ax] > 0 && lo < v && lo <= hi) m |= 1u << (2 * ax);
-          if (co[ax] < N - 1 && hi < v && hi <= lo) m |= 1u << (2 * ax + 1);
+          if (co[ax] > 0 && lo < v && lo <= hi && !(up[r - sl[ax]] & 0x80)) m |= 1u << (2 * ax);
+          if (co[ax] < N - 1 && hi < v && hi <= lo && !(up[r + sl[ax]] & 0x80))
+            m |= 1u << (2 * ax + 1);
         }
       }
-      up[r] = (unsigned char)m;
+      up[r] = (unsigned char)(m | (fixed ? 0x80u : 0u));  // bit 7 stays as read
       if (m) {
         atomicAdd(&indeg[r >> 2], (unsigned)__popc(m) << (8 * (r & 3)));
-      } else {
+      } else if (!fixed) {
         const unsigned act = __activemask();  // warp-aggregated append
         const int leader = __ffs(act) - 1, lane = threadIdx.x & 31;
         int base = 0;
@@ -621,9 +632,9 @@ __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int 
     if (ok) {
       unsigned short* off = c.lev_off + (size_t)g * (kMaxLevels + 1);
       for (int l = threadIdx.x; l < depth; l += blockDim.x) off[l] = offs[l];
-      if (threadIdx.x == 0) off[depth] = (unsigned short)N3;
+      if (threadIdx.x == 0) off[depth] = (unsigned short)lo;
       unsigned short* perm = c.lev_perm + (size_t)g * N3;
-      for (int e = threadIdx.x; e < N3; e += blockDim.x) perm[e] = lst[e];
+      for (int e = threadIdx.x; e < lo; e += blockDim.x) perm[e] = lst[e];
     }
     __syncthreads();  // shared arrays are reused by the next cell
   }

@@ -204,7 +204,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
 
 // Level-pass helpers (min mode, Alg. 2).  During the level pass bits 16-31
 // of a node's flag word hold the step in which the pass took it (kNotTaken
-// before, and for fixed nodes, which are in no level).  take_node: no other
+// before, and for the filler of partial cells, which is in no level).  take_node: no other
 // thread writes node si's flag word in this step: record the step, clear the
 // active bit, recompute the node from its six neighbours (Eq. 2), store a
 // lower value and mark a change by more than kappa (kBig).
@@ -277,7 +277,7 @@ __device__ __forceinline__ void level_check(const T* __restrict__ U, unsigned* _
 }
 
 // One pass over a cell's nodes in the level order of its table (see
-// polish_levels_kernel; fixed nodes are in no level): level by level, every
+// polish_levels_kernel; the filler is in no level): level by level, every
 // node of a level is taken (a first visit starts with no node active), in
 // steps of UNR nodes a thread split by a barrier.  A node's FP32 upwind
 // neighbours have smaller levels, so where the FP64 values keep the FP32

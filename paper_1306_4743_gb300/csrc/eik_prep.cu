@@ -533,14 +533,14 @@ __global__ void polish_graph_kernel(const PolishInstance* __restrict__ pi,
 // no in-cell upwind neighbour, and a node joins the layer after the one in
 // which its last upwind neighbour was taken (so level = longest upwind
 // chain).  Each layer is appended to the node list in shared memory and
-// becomes a run of lev_perm; lev_off[l] is where layer l starts.  Fixed
-// nodes (exits and the filler of partial cells, s = +inf) are in no layer
-// and are no node's upwind neighbour: their values never change, so
-// lev_off[depth] is the number of nodes the pass computes.  One block per
-// cell; cells deeper than kMaxLevels - 1 get no table (lev_depth 0).
+// becomes a run of lev_perm; lev_off[l] is where layer l starts.  The
+// filler of partial cells is in no layer (lev_off[depth] counts the cell's
+// grid nodes); exit nodes are in layer 0, where the pass takes them without
+// computing (their s is +inf).  One block per cell; cells deeper than
+// kMaxLevels - 1 get no table (lev_depth 0).
 __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int total_cells,
                                      CellArrays c) {
-  __shared__ unsigned char up[4096];   // bit 2a: -axis a neighbour upwind, 2a + 1: +axis a; bit 7: fixed
+  __shared__ unsigned char up[4096];   // bit 2a: -axis a neighbour upwind, 2a + 1: +axis a
   __shared__ unsigned indeg[1024];     // upwind neighbours not yet taken, a byte per node
   __shared__ unsigned short lst[4096];  // nodes in level order
   __shared__ unsigned short offs[kMaxLevels + 1];
@@ -556,33 +556,28 @@ __global__ void polish_levels_kernel(const PolishInstance* __restrict__ pi, int 
     if (threadIdx.x == 0) tail = 0;
     for (int w = threadIdx.x; w < (N3 + 3) / 4; w += blockDim.x) indeg[w] = 0u;
     __syncthreads();
-    // bit 7 of up[]: the node is fixed
-    const double* sc = s64 + (long long)lc * N3;
-    for (int r = threadIdx.x; r < N3; r += blockDim.x)
-      up[r] = sc[r] < CUDART_INF ? (unsigned char)0 : (unsigned char)0x80;
-    __syncthreads();
     for (int r = threadIdx.x; r < N3; r += blockDim.x) {
       const int a = r & nm, b = (r >> lg) & nm, cc = r >> (2 * lg);
+      // the filler of a partial cell lies outside the grid; it holds +inf, so
+      // it is no node's upwind neighbour either
+      const bool filler = N * cx + a >= P.nx || N * cy + b >= P.ny || N * cz + cc >= P.nz;
       unsigned m = 0;
-      const bool fixed = (up[r] & 0x80) != 0;
-      if (!fixed) {
+      if (!filler && s64[(long long)lc * N3 + r] < CUDART_INF) {
         const long long t = (long long)(N * cx + a + 1) + sy * (N * cy + b + 1) + sz * (N * cz + cc + 1);
         const float v = u32[t];
         const int co[3] = {a, b, cc};
         const long long st[3] = {1, sy, sz};
-        const int sl[3] = {1, N, N * N};
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
           const float lo = u32[t - st[ax]], hi = u32[t + st[ax]];
-          if (co[ax] > 0 && lo < v && lo <= hi && !(up[r - sl[ax]] & 0x80)) m |= 1u << (2 * ax);
-          if (co[ax] < N - 1 && hi < v && hi <= lo && !(up[r + sl[ax]] & 0x80))
-            m |= 1u << (2 * ax + 1);
+          if (co[ax] > 0 && lo < v && lo <= hi) m |= 1u << (2 * ax);
+          if (co[ax] < N - 1 && hi < v && hi <= lo) m |= 1u << (2 * ax + 1);
         }
       }
-      up[r] = (unsigned char)(m | (fixed ? 0x80u : 0u));  // bit 7 stays as read
+      up[r] = (unsigned char)m;
       if (m) {
         atomicAdd(&indeg[r >> 2], (unsigned)__popc(m) << (8 * (r & 3)));
-      } else if (!fixed) {
+      } else if (!filler) {
         const unsigned act = __activemask();  // warp-aggregated append
         const int leader = __ffs(act) - 1, lane = threadIdx.x & 31;
         int base = 0;

@@ -125,11 +125,14 @@ __device__ __forceinline__ bool worker_any(int worker, bool pred) {
 // `left` counts, per axis (bits 0-9 x, 10-19 y, 20-29 z), the activations of
 // neighbours on the plane the sweep has just left (at most one per node and
 // axis, and a thread takes at most 2 (3n - 2) nodes of a sweep, so a field
-// cannot overflow).
+// cannot overflow).  `hi` packs the largest in-grid local index per axis
+// (bits 0-7 x, 8-15 y, 16-23 z): the filler of a partial cell is never
+// activated (it is fixed; a filler node left behind a sweep would cost one
+// more sweep to clear).
 template <typename T, int N, bool REPLACE>
 __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restrict__ S,
                                             unsigned* __restrict__ chg, int si, int fx, int fy,
-                                            int fz, T kappa, unsigned& n_updates,
+                                            int fz, int hi, T kappa, unsigned& n_updates,
                                             unsigned& left) {
   using G = Geo<T, N>;
   const int i = si % N, j = (si / N) % N, k = si / (N * N);
@@ -177,7 +180,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
         activate(si - 1);
         left += fx == 0 ? 1u : 0u;
       }
-      if (i < N - 1 && uses(xp)) {
+      if (i < (hi & 0xff) && uses(xp)) {
         activate(si + 1);
         left += fx != 0 ? 1u : 0u;
       }
@@ -185,7 +188,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
         activate(si - N);
         left += fy == 0 ? (1u << 10) : 0u;
       }
-      if (j < N - 1 && uses(yp)) {
+      if (j < ((hi >> 8) & 0xff) && uses(yp)) {
         activate(si + N);
         left += fy != 0 ? (1u << 10) : 0u;
       }
@@ -193,7 +196,7 @@ __device__ __forceinline__ void update_node(T* __restrict__ U, const T* __restri
         activate(si - N * N);
         left += fz == 0 ? (1u << 20) : 0u;
       }
-      if (k < N - 1 && uses(zp)) {
+      if (k < (hi >> 16) && uses(zp)) {
         activate(si + N * N);
         left += fz != 0 ? (1u << 20) : 0u;
       }
@@ -405,7 +408,7 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
                                                const unsigned short* __restrict__ tab,
                                                const int* __restrict__ off,
                                                unsigned short* __restrict__ list, int dir,
-                                               int first, int last, int tid, int worker,
+                                               int first, int last, int hi, int tid, int worker,
                                                T kappa, unsigned& n_updates, int* ws) {
   using G = Geo<T, N>;
   constexpr int NT = WPC * 32;
@@ -462,7 +465,8 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
       for (int h = 0; h < UNR; ++h) {
         if (!act[h]) continue;
         did = true;
-        update_node<T, N, REPLACE>(U, S, chg, (int)cur[h], fx, fy, fz, kappa, n_updates, left);
+        update_node<T, N, REPLACE>(U, S, chg, (int)cur[h], fx, fy, fz, hi, kappa, n_updates,
+                                   left);
       }
       // also ends the plane; before the last initially active plane the
       // sweep cannot end, so a plain barrier does (bar.sync costs about half
@@ -490,7 +494,7 @@ __device__ __forceinline__ unsigned sweep_cell(T* __restrict__ U, const T* __res
         for (int h = 0; h < UNR; ++h) {
           const int x = x0 + h * NT;
           if (x >= total) break;
-          update_node<T, N, REPLACE>(U, S, chg, (int)list[x], fx, fy, fz, kappa, n_updates,
+          update_node<T, N, REPLACE>(U, S, chg, (int)list[x], fx, fy, fz, hi, kappa, n_updates,
                                      left);
         }
       }
@@ -588,6 +592,9 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
     const int cy = (lc / I.ncx) % I.ncy;
     const int cz = lc / (I.ncx * I.ncy);
     const T kappa = (T)(p.kappa_from_ctl ? ctl->kappa_bulk : I.kappa);
+    // largest in-grid local index per axis (the rest of a partial cell is filler)
+    const int hi_ext = (min(N, I.nx - N * cx) - 1) | ((min(N, I.ny - N * cy) - 1) << 8) |
+                       ((min(N, I.nz - N * cz) - 1) << 16);
 
     // ---- 2. stage cell + halo ------------------------------------------
     // (and, for the level pass of the polish, the cell's level table)
@@ -680,7 +687,9 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
           else { i = a; j = b; k = side; }
           const int e = i + N * (j + N * k);
           const int t = (i + 1) + G::SY * (j + 1) + G::SZ * (k + 1);
-          if (REPLACE || vlt(U[side ? t + step : t - step], U[t])) chg[e] = kActive;
+          const bool in_grid =
+              i <= (hi_ext & 0xff) && j <= ((hi_ext >> 8) & 0xff) && k <= (hi_ext >> 16);
+          if (in_grid && (REPLACE || vlt(U[side ? t + step : t - step], U[t]))) chg[e] = kActive;
         }
       }
       worker_sync<WPC>(worker);
@@ -728,8 +737,9 @@ __global__ void __launch_bounds__(WPC * 32 * WORKERS)
         lm = 0;  // nothing active: converged without a sweep
         return;
       }
-      lm = sweep_cell<T, N, WPC, REPLACE, COMPACT>(U, S, chg, tab, off, list, d, first, last, tid,
-                                                   worker, kappa, n_updates, wshared + 32);
+      lm = sweep_cell<T, N, WPC, REPLACE, COMPACT>(U, S, chg, tab, off, list, d, first, last,
+                                                   hi_ext, tid, worker, kappa, n_updates,
+                                                   wshared + 32);
       ++nsw;
     };
     if constexpr (!REPLACE) {

@@ -183,3 +183,26 @@ def test_batch_graph_replay_reads_current_inputs(eik, torch):
         outs, st = s.solve_batch_device(bt, outs=outs)
         assert rel_err(outs[0].cpu().numpy(), p2) <= 1e-9
         assert rel_err(outs[1].cpu().numpy(), probs[1]) <= 1e-9
+
+
+@pytest.mark.parametrize("make", [lambda: W.oscillatory(65), lambda: W.barrier_blocks(65)],
+                         ids=["oscillatory65", "barrier65"])
+def test_bulk_threshold_from_the_field(eik, make):
+    """The FP32 bulk threshold chosen per solve (bulk_kappa_rel = 0) is
+    3e-3 r^2 (at most 1) cell edges of front slowness, r = mean(s) mean(1/s)
+    over the non-exit nodes, s = h / F; a given factor is used as it is; the
+    result meets the FP32 + polish bound either way."""
+    p = make()
+    s = p.h / p.F[p.mask == 0].astype(np.float64)
+    r = float(np.mean(s) * np.mean(1.0 / s))
+    s_front = 1.0 / float(np.mean(1.0 / s))
+    for rel in (0.0, 0.05):
+        with eik.Solver(precision="fp32_polish", bulk_kappa_rel=rel) as sv:
+            u, st = sv.solve(p.F, p.mask, p.q, p.h, tol=1e-12)
+        factor = rel if rel > 0 else min(3e-3 * r * r, 1.0)
+        want = factor * st["cell_n_used"] * s_front
+        assert st["bulk_kappa"] == pytest.approx(want, rel=1e-3), (rel, r)
+        assert rel_err(u, p) <= TOL["fp32_polish"]
+    with eik.Solver(precision="fp64") as sv:
+        _, st = sv.solve(p.F, p.mask, p.q, p.h, tol=1e-12)
+    assert st["bulk_kappa"] == 0.0
